@@ -1,0 +1,149 @@
+/*
+ * hs.h -- C ABI of the GB300 moving-PML sweeping preconditioner library (libhs.so).
+ *
+ * The library solves the 2D PML-stretched Helmholtz equation discretised by
+ * the 5-point scheme of Engquist & Ying (2010), Sec. 2.1, Eq. helmd:
+ *
+ *   Delta u + omega^2 / c^2(x) u = f   on (0,1)^2, PML on all four sides,
+ *
+ * on the grid p_ij = (ih, jh), h = 1/(n+1), 1 <= i, j <= n, preconditioned by
+ * the approximate sweeping factorisation with moving PMLs (Sec. 2.2-2.3,
+ * Algorithms 3 and 4, two fronts, d layers per step).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Vectors.  Complex, interleaved (re, im).  One right-hand side (RHS) is a
+ *   contiguous n*n array in the paper's ordering (x1 fastest, row by row in
+ *   x2, Sec. 2.1); RHS r starts at element r*n*n.  dtype HS_C64 means
+ *   float2 elements, HS_C128 double2 elements.
+ * Pointers.  Vector pointers are DEVICE pointers unless stated otherwise; the
+ *   caller owns them.  The plan owns every factor and workspace buffer.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  All work of a call is enqueued on that stream; calls return
+ *   after enqueueing except where stated.
+ * Errors.  Every entry point returns an hs_status.  Asynchronous device
+ *   errors (pivot breakdown, expired bounded waits) are recorded in a status
+ *   word of the plan and reported by the next synchronising call
+ *   (hs_solve, hs_sync) or by hs_last_device_status().  Nothing throws.
+ */
+#ifndef HS_H_
+#define HS_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HS_OK = 0,
+  HS_EINVAL = 1,       /* invalid argument: even n, widths too large, NULL pointer, nrhs out of range */
+  HS_ENOMEM = 2,       /* device allocation failed */
+  HS_EBREAKDOWN = 3,   /* zero pivot while inverting a diagonal block of a subproblem factor */
+  HS_ETIMEOUT = 4,     /* a bounded device-side wait (TMA barrier) expired */
+  HS_ENOCONV = 5,      /* FGMRES did not reach the tolerance within maxit, or produced NaN */
+  HS_ECUDA = 6,        /* CUDA runtime error */
+  HS_EUNSUPPORTED = 7  /* configuration outside what the kernels are built for */
+} hs_status;
+
+enum { HS_C64 = 64, HS_C128 = 128 };
+
+/* Tuning and method constants.  hs_default_options() fills the defaults. */
+typedef struct {
+  double alpha;          /* alpha of Eq. helmalpha: the subproblems use (omega + i alpha)^2 / c^2.   default 2 */
+  double pml_C;          /* C of Eq. sigma (PML strength, same for boundary and moving PMLs).         default 20 */
+  int layers_per_step;   /* d of Sec. 2.3 (rows eliminated per sweep step).                           default 12 */
+  int factor_prec;       /* HS_C64: complex float factors and sweep; HS_C128: complex double.          default HS_C64 */
+  int chunk;             /* x1 columns per partition chunk of the subproblem solves (>= 2; 0 = auto). default 0 */
+  int max_nrhs;          /* largest nrhs any later call will use (workspace is sized at setup).       default 64 */
+  int restart;           /* FGMRES restart length m.                                                  default 20 */
+  int reorth;            /* 0: classical Gram-Schmidt; 1: CGS with a second pass when needed (DGKS).  default 1 */
+  long long spin_budget; /* SM clock cycles a device-side barrier wait may take before HS_ETIMEOUT.   default 1<<30 */
+} hs_options;
+
+typedef struct hs_plan hs_plan;
+
+/* Per-solve report, filled by hs_solve (host memory owned by the caller). */
+typedef struct {
+  int iterations;        /* FGMRES iterations (Arnoldi steps) until the last RHS converged */
+  int restarts;          /* restart cycles started */
+  int applies;           /* preconditioner applications (each over all nrhs) */
+  double max_relres;     /* max over RHS of the final FP64 true relative residual ||f - A u|| / ||f|| */
+  double t_apply_ms;     /* device time spent in M_alpha applications */
+  double t_matvec_ms;    /* device time in A z products */
+  double t_orth_ms;      /* device time in Gram-Schmidt and updates */
+  double t_total_ms;     /* wall time of the call */
+} hs_solve_info;
+
+/* Fill *opt with the defaults listed above.  Returns HS_EINVAL if opt is NULL. */
+int hs_default_options(hs_options* opt);
+
+/*
+ * hs_setup -- build the sweeping factorisation (Algorithm 3, Sec. 2.3).
+ *
+ * c        HOST pointer to n*n velocities c(ih, jh) (double, x1 fastest), c > 0.
+ * omega    angular frequency omega > 0 (Sec. 1).
+ * n        grid points per axis; odd, so that the two fronts meet at the middle
+ *          layer (n+1)/2 (Sec. 2.3).
+ * dim      2 (3D plans are not built by this entry point: HS_EUNSUPPORTED).
+ * pml_width         b_p: boundary PML width in grid points, eta = b_p h (Eq. sigma).
+ * moving_pml_width  b: moving PML width in grid points (Eq. helma), 1 <= b <= b_p + 1.
+ * opt      NULL for defaults.
+ * stream   stream for the setup kernels; the call synchronises it before returning.
+ * out      receives the plan.
+ *
+ * Every subproblem H_m (the front F, the end E, every d-layer block of both
+ * fronts and the middle layer) is factored in one batched launch; windows
+ * taller than 32 rows return HS_EUNSUPPORTED.  HS_EBREAKDOWN reports a zero
+ * pivot.  The plan keeps a copy of c; the caller may free it after return.
+ */
+int hs_setup(const double* c, double omega, int n, int dim, int pml_width, int moving_pml_width,
+             const hs_options* opt, void* stream, hs_plan** out);
+
+/*
+ * hs_apply -- z = M_alpha r (Algorithm 4 with two fronts, Sec. 2.3).
+ * r, z     device vectors of nrhs RHS (layout above), dtype HS_C64 or HS_C128;
+ *          r and z may alias.  1 <= nrhs <= opt.max_nrhs.
+ * The sweep runs in the plan's factor precision; dtype only sets the I/O type.
+ */
+int hs_apply(hs_plan* plan, const void* r, void* z, int nrhs, int dtype, void* stream);
+
+/*
+ * hs_matvec -- y = A x with the Eq. helmd operator (alpha = 0).
+ * dtype HS_C128 computes in FP64, HS_C64 in FP32.  x and y must not alias.
+ */
+int hs_matvec(hs_plan* plan, const void* x, void* y, int nrhs, int dtype, void* stream);
+
+/*
+ * hs_solve -- solve A u = f for nrhs RHS with right-preconditioned flexible
+ * GMRES(m) (Sec. 2.3 uses GMRES on M_alpha A; the flexible right form lets the
+ * true residual decide): FP64 Arnoldi (Gram-Schmidt) and true residual,
+ * preconditioner in the plan's factor precision.  The RHS advance in lock
+ * step; each stops when ||f - A u|| <= tol ||f|| (FP64, recomputed at every
+ * restart and at the end).
+ * f, u     device HS_C128 vectors; u is the initial guess on entry and the
+ *          solution on return.
+ * tol      relative residual tolerance (> 0).  maxit: max Arnoldi steps.
+ * info     optional host struct (may be NULL).
+ * Synchronises `stream`.  Returns HS_ENOCONV if some RHS did not converge.
+ */
+int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double tol, int maxit,
+             hs_solve_info* info, void* stream);
+
+/* Wait for the plan's work on `stream` and report any recorded device error. */
+int hs_sync(hs_plan* plan, void* stream);
+
+/* Status recorded by device kernels since setup (HS_OK if none). */
+int hs_last_device_status(hs_plan* plan);
+
+/* Bytes of device memory owned by the plan. */
+long long hs_plan_bytes(const hs_plan* plan);
+
+/* Free the plan and all device memory it owns.  NULL is accepted. */
+int hs_destroy(hs_plan* plan);
+
+/* Static description of a status code. */
+const char* hs_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HS_H_ */

@@ -26,7 +26,9 @@ path, chosen independently there):
     PML on all sides); s uses the real omega; alpha only shifts the mass term;
   - the moving profile uses eta_b = b h with the same constant C as the
     boundary PML; the block window for d > 1 is the block rows plus b - 1
-    rows on the eliminated side; the middle block gets both profiles;
+    rows on the eliminated side; the middle is the single layer (n+1)/2 with
+    both profiles, and the last block of each front takes the remainder
+    rows when d does not divide them;
   - the half band width of P_m H_m P_m^t is the window height (the paper's
     "b - 1 diagonals" is an off-by-one);
   - the LAPACK band LU pivots by rows; any exact solver defines the same T~.
@@ -62,27 +64,37 @@ class Block:
 def partition(n, bp, b, dL, full_window=False):
     """Two-front block partition of Sec. 2.3 (Fig. 2 left and right).
 
+    The fronts sweep from F = rows 1..bp upward and from E = rows
+    n-bp+1..n downward and meet at the middle layer (n+1)/2, which the paper
+    visits last with moving PMLs on both sides.  Each front eliminates d
+    rows per step; the rows between F and the middle layer number
+    (n-1)/2 - bp, and when d does not divide them the last block of each
+    front takes the remainder.
+
     Returns (lower, upper, middle): ``lower`` = [F, B_1, ..., B_K] in sweep
-    order, ``upper`` = [E, B'_1, ..., B'_K], ``middle`` = the centre block.
-    K = floor(((n+1)/2 - 1 - bp)/dL).  With ``full_window`` every window
-    extends to the domain boundary on its eliminated side (exact-limit test
-    knob: then T~_B equals the exact Schur inverse, Sec. 2.2).
+    order, ``upper`` = [E, B'_1, ..., B'_K], ``middle`` = the middle layer.
+    With ``full_window`` every window extends to the domain boundary on its
+    eliminated side (exact-limit test knob: then T~_B equals the exact Schur
+    inverse, Sec. 2.2).
     """
     if n % 2 != 1 or n < 2 * bp + 1 or bp < 1 or dL < 1 or b < 1 or b > bp + 1:
         raise ValueError("invalid partition parameters")
-    K = ((n + 1) // 2 - 1 - bp) // dL
+    rows_front = (n - 1) // 2 - bp
+    sizes = [dL] * (rows_front // dL) + ([rows_front % dL] if rows_front % dL else [])
     lower = [Block("F", 1, bp, 1, bp)]
     upper = [Block("E", n - bp + 1, n, n - bp + 1, n)]
-    for k in range(1, K + 1):
-        lo, hi = bp + (k - 1) * dL + 1, bp + k * dL
+    lo = bp + 1
+    for d in sizes:
+        hi = lo + d - 1
         lower.append(Block("lower", lo, hi, 1 if full_window else lo - b + 1, hi))
-        lo, hi = n - bp - k * dL + 1, n - bp - (k - 1) * dL
-        upper.append(Block("upper", lo, hi, lo, n if full_window else hi + b - 1))
-    lo, hi = bp + K * dL + 1, n - bp - K * dL
+        ulo, uhi = n + 1 - hi, n + 1 - lo
+        upper.append(Block("upper", ulo, uhi, ulo, n if full_window else uhi + b - 1))
+        lo = hi + 1
+    m = (n + 1) // 2
     if full_window:
-        middle = Block("middle", lo, hi, 1, n)
+        middle = Block("middle", m, m, 1, n)
     else:
-        middle = Block("middle", lo, hi, lo - b + 1, hi + b - 1)
+        middle = Block("middle", m, m, m - b + 1, m + b - 1)
     return lower, upper, middle
 
 

@@ -1,0 +1,107 @@
+// Device helpers of libhs: 1D TMA bulk copies into shared memory completed on
+// an mbarrier, bounded barrier waits, and the plan's device status word.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "hs_internal.cuh"
+
+namespace hs {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Arrive once on `bar` and announce `bytes` of asynchronous transactions.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
+// global to this CTA's shared memory; completion is signalled on `bar`.
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of `bar` for at most `budget` clock cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long budget) {
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Record the first error of the plan: code, block, column.
+__device__ __forceinline__ void set_status(int* status, int code, int block, int col) {
+  if (atomicCAS(status, 0, code) == 0) {
+    status[1] = block;
+    status[2] = col;
+  }
+}
+
+template <typename R> struct Shfl;
+template <> struct Shfl<float> {
+  static __device__ __forceinline__ float get(float v, int src, int width = 32) {
+    return __shfl_sync(0xffffffffu, v, src, width);
+  }
+  static __device__ __forceinline__ float xr(float v, int m, int width = 32) {
+    return __shfl_xor_sync(0xffffffffu, v, m, width);
+  }
+};
+template <> struct Shfl<double> {
+  static __device__ __forceinline__ double get(double v, int src, int width = 32) {
+    return __shfl_sync(0xffffffffu, v, src, width);
+  }
+  static __device__ __forceinline__ double xr(double v, int m, int width = 32) {
+    return __shfl_xor_sync(0xffffffffu, v, m, width);
+  }
+};
+template <typename R> __device__ __forceinline__ cplx<R> shfl_c(cplx<R> v, int src, int width = 32) {
+  return cplx<R>{Shfl<R>::get(v.re, src, width), Shfl<R>::get(v.im, src, width)};
+}
+template <typename R> __device__ __forceinline__ cplx<R> shfl_xor_c(cplx<R> v, int m, int width = 32) {
+  return cplx<R>{Shfl<R>::xr(v.re, m, width), Shfl<R>::xr(v.im, m, width)};
+}
+
+// Number of complex elements of one column payload of a block's factor:
+// G (W x (W+1), padded rows), V (d_out x (W+1)), c (W), rounded up to an even
+// count so that every payload is a multiple of 16 bytes.
+__host__ __device__ __forceinline__ long long payload_elems(int W, int d_out) {
+  long long e = (long long)(W + d_out) * (W + 1) + W;
+  return (e + 1) & ~1LL;
+}
+// Reduced-system factors per separator: Gamma and F, each W x (W+1).
+__host__ __device__ __forceinline__ long long red_elems(int W) { return 2LL * W * (W + 1); }
+// Corner blocks per interior chunk: G_r, W_l, W_r, each W x (W+1).
+__host__ __device__ __forceinline__ long long cor_elems(int W) { return 3LL * W * (W + 1); }
+
+}  // namespace hs

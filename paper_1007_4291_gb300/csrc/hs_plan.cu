@@ -1,0 +1,316 @@
+// Host side of libhs: option defaults, argument checks, the two-front block
+// partition (Sec. 2.3), the PML tables (Eq. sigma and the stretch factors of
+// Sec. 2.1, the moving profile of Eq. helma), device memory of the plan, and
+// the status/error entry points.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <complex>
+#include "hs_internal.cuh"
+#include "hs_device.cuh"
+
+namespace hs {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return HS_ENOMEM; }
+  return HS_ECUDA;
+}
+
+int padded_width(int w) {
+  if (w <= 0) return -1;
+  if (w <= 8) return 8;
+  if (w <= 12) return 12;
+  if (w <= 16) return 16;
+  if (w <= 24) return 24;
+  if (w <= 32) return 32;
+  return -1;
+}
+
+namespace {
+
+using zc = std::complex<double>;
+
+// Eq. sigma, two-sided quadratic ramp of width eta on [0,1].
+double sigma_boundary(double t, double eta, double C) {
+  if (t <= eta) { double q = (t - eta) / eta; return (C / eta) * q * q; }
+  if (t >= 1.0 - eta) { double q = (t - 1.0 + eta) / eta; return (C / eta) * q * q; }
+  return 0.0;
+}
+// One-sided moving profile of Eq. helma: distance d from the window's
+// Dirichlet row, width eta_b; zero from depth eta_b on.
+double sigma_moving(double d, double eta_b, double C) {
+  if (d < 0.0 || d > eta_b) return 0.0;
+  double q = (d - eta_b) / eta_b;
+  return (C / eta_b) * q * q;
+}
+// 1/s = 1 + i sigma/omega (Sec. 2.1)
+zc inv_stretch(double sig, double omega) { return zc(1.0, sig / omega); }
+zc stretch(double sig, double omega) { return 1.0 / inv_stretch(sig, omega); }
+
+c128 to_c(zc z) { return c128{z.real(), z.imag()}; }
+c64 to_f(zc z) { return c64{(float)z.real(), (float)z.imag()}; }
+
+template <typename T> int dalloc(Plan& p, T** ptr, size_t count) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e != cudaSuccess) { *ptr = nullptr; return cuda_status(e); }
+  p.bytes += (long long)bytes;
+  return HS_OK;
+}
+#define HS_TRY(expr) do { int _s = (expr); if (_s != HS_OK) return _s; } while (0)
+
+// Two-front partition: F, d-row lower blocks (last one takes the remainder),
+// the middle layer (n+1)/2, and the mirrored upper front ending at E.
+void build_blocks(Plan& p) {
+  const int n = p.n, bp = p.bp, b = p.b, dL = p.dL;
+  const int m = (n + 1) / 2;
+  const int rows_front = (n - 1) / 2 - bp;
+  std::vector<int> sizes;
+  for (int r = rows_front; r > 0; r -= std::min(dL, r)) sizes.push_back(std::min(dL, r));
+  p.blocks.clear();
+  p.stages.clear();
+  auto add = [&](BlockDesc d) { p.blocks.push_back(d); return (int)p.blocks.size() - 1; };
+  BlockDesc F{}; F.kind = BK_F; F.lo = 1; F.hi = bp; F.wlo = 1; F.whi = bp;
+  F.prev_lo_row = 0; F.prev_hi_row = 0; F.next_row = bp + 1; F.coup_local = bp - 1;
+  BlockDesc E{}; E.kind = BK_E; E.lo = n - bp + 1; E.hi = n; E.wlo = n - bp + 1; E.whi = n;
+  E.prev_lo_row = 0; E.prev_hi_row = 0; E.next_row = n - bp; E.coup_local = 0;
+  p.stages.push_back({add(F), add(E)});
+  int lo = bp + 1;
+  for (int d : sizes) {
+    int hi = lo + d - 1;
+    BlockDesc Lb{}; Lb.kind = BK_LOWER; Lb.lo = lo; Lb.hi = hi; Lb.wlo = lo - b + 1; Lb.whi = hi;
+    Lb.prev_lo_row = lo - 1; Lb.prev_hi_row = 0; Lb.next_row = hi + 1; Lb.coup_local = hi - Lb.wlo;
+    int ulo = n + 1 - hi, uhi = n + 1 - lo;
+    BlockDesc Ub{}; Ub.kind = BK_UPPER; Ub.lo = ulo; Ub.hi = uhi; Ub.wlo = ulo; Ub.whi = uhi + b - 1;
+    Ub.prev_lo_row = 0; Ub.prev_hi_row = uhi + 1; Ub.next_row = ulo - 1; Ub.coup_local = 0;
+    p.stages.push_back({add(Lb), add(Ub)});
+    lo = hi + 1;
+  }
+  BlockDesc M{}; M.kind = BK_MIDDLE; M.lo = m; M.hi = m; M.wlo = m - b + 1; M.whi = m + b - 1;
+  M.prev_lo_row = m - 1; M.prev_hi_row = m + 1; M.next_row = 0; M.coup_local = -1;
+  p.middle = add(M);
+  for (auto& d : p.blocks) {
+    d.w = d.whi - d.wlo + 1;
+    d.W = padded_width(d.w);
+    d.out_off = d.lo - d.wlo;
+    d.d_out = d.hi - d.lo + 1;
+  }
+}
+
+}  // namespace
+}  // namespace hs
+
+using namespace hs;
+
+extern "C" int hs_default_options(hs_options* opt) {
+  if (!opt) return HS_EINVAL;
+  opt->alpha = 2.0;
+  opt->pml_C = 20.0;
+  opt->layers_per_step = 12;
+  opt->factor_prec = HS_C64;
+  opt->chunk = 0;
+  opt->max_nrhs = 64;
+  opt->restart = 20;
+  opt->reorth = 1;
+  opt->spin_budget = 1LL << 30;
+  return HS_OK;
+}
+
+extern "C" const char* hs_strerror(int s) {
+  switch (s) {
+    case HS_OK: return "success";
+    case HS_EINVAL: return "invalid argument";
+    case HS_ENOMEM: return "device allocation failed";
+    case HS_EBREAKDOWN: return "zero pivot in a subproblem factorisation";
+    case HS_ETIMEOUT: return "bounded device wait expired";
+    case HS_ENOCONV: return "FGMRES did not converge";
+    case HS_ECUDA: return "CUDA runtime error";
+    case HS_EUNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+static void free_plan_memory(Plan* p) {
+  void* ptrs[] = {p->d_inv_s1, p->d_a1, p->d_inv_s2, p->d_a2, p->f_inv_s1, p->f_a1, p->f_inv_s2, p->f_a2,
+                  p->d_pml1, p->d_pml2, p->d_m0, p->f_m0, p->d_cinv2, p->d_s2win, p->d_blocks,
+                  p->d_fac, p->d_red, p->d_cor, p->d_u, p->d_z, p->d_rc, p->d_lc, p->d_xs, p->d_ps,
+                  p->d_status, p->d_V, p->d_Zk, p->d_w, p->d_x, p->d_f, p->d_part, p->d_h, p->d_nrm};
+  for (void* q : ptrs) if (q) cudaFree(q);
+}
+
+extern "C" int hs_destroy(hs_plan* plan) {
+  if (!plan) return HS_OK;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  cudaDeviceSynchronize();
+  free_plan_memory(p);
+  delete p;
+  return HS_OK;
+}
+
+extern "C" long long hs_plan_bytes(const hs_plan* plan) {
+  if (!plan) return 0;
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  return p->bytes + p->kry_bytes;
+}
+
+extern "C" int hs_last_device_status(hs_plan* plan) {
+  if (!plan) return HS_EINVAL;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  int st[3] = {0, 0, 0};
+  if (cudaMemcpy(st, p->d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return HS_ECUDA;
+  return st[0];
+}
+
+extern "C" int hs_sync(hs_plan* plan, void* stream) {
+  if (!plan) return HS_EINVAL;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  return hs_last_device_status(plan);
+}
+
+extern "C" int hs_setup(const double* c, double omega, int n, int dim, int pml_width, int moving_pml_width,
+                        const hs_options* opt_in, void* stream, hs_plan** out) {
+  if (!out) return HS_EINVAL;
+  *out = nullptr;
+  if (!c || !(omega > 0.0) || !std::isfinite(omega)) return HS_EINVAL;
+  if (dim != 2) return (dim == 3) ? HS_EUNSUPPORTED : HS_EINVAL;
+  if (n < 3 || n % 2 != 1 || pml_width < 1 || 2 * pml_width + 1 > n) return HS_EINVAL;
+  if (moving_pml_width < 1 || moving_pml_width > pml_width + 1) return HS_EINVAL;
+  hs_options opt;
+  hs_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (!(opt.alpha >= 0.0) || !(opt.pml_C >= 0.0) || opt.layers_per_step < 1 || opt.max_nrhs < 1 ||
+      opt.max_nrhs > 4096 || opt.restart < 1 || opt.chunk < 0 || opt.chunk == 1 || opt.spin_budget < 1)
+    return HS_EINVAL;
+  if (opt.factor_prec != HS_C64 && opt.factor_prec != HS_C128) return HS_EINVAL;
+  for (long long k = 0; k < (long long)n * n; ++k)
+    if (!(c[k] > 0.0) || !std::isfinite(c[k])) return HS_EINVAL;
+
+  Plan* p = new Plan();
+  p->n = n; p->dim = dim; p->bp = pml_width; p->b = moving_pml_width; p->dL = opt.layers_per_step;
+  p->omega = omega; p->alpha = opt.alpha; p->C = opt.pml_C; p->h = 1.0 / (n + 1);
+  p->prec = opt.factor_prec; p->max_nrhs = opt.max_nrhs; p->opt = opt;
+  build_blocks(*p);
+  int Wmax = 0;
+  for (auto& d : p->blocks) {
+    if (d.W < 0) { delete p; return HS_EUNSUPPORTED; }
+    Wmax = std::max(Wmax, d.W);
+  }
+  // x1 chunking of the subproblem solves (>= 2 columns per chunk).
+  p->L = opt.chunk ? opt.chunk : 32;
+  if (p->L > n) p->L = n;
+  if (p->L < 2) p->L = 2;
+  p->P = (n + p->L - 1) / p->L;
+
+  int st = HS_OK;
+  auto fail = [&](int s) { free_plan_memory(p); delete p; return s; };
+  const double h = p->h, eta = p->bp * h, eta_b = p->b * h, C = p->C;
+
+  // ---- 1D tables of the x1 and x2 axes (Eq. sigma, both axes two-sided)
+  std::vector<c128> inv_s(n + 2), a_half(n + 1);
+  std::vector<c64> f_inv_s(n + 2), f_a_half(n + 1);
+  std::vector<unsigned char> pml(n + 2, 0);
+  for (int k = 0; k <= n + 1; ++k) {
+    zc v = inv_stretch(sigma_boundary(k * h, eta, C), omega);
+    inv_s[k] = to_c(v); f_inv_s[k] = to_f(v);
+  }
+  for (int k = 0; k <= n; ++k) {
+    zc v = stretch(sigma_boundary((k + 0.5) * h, eta, C), omega) / (h * h);
+    a_half[k] = to_c(v); f_a_half[k] = to_f(v);
+  }
+  for (int k = 1; k <= n; ++k) {
+    bool t = sigma_boundary(k * h, eta, C) != 0.0 || sigma_boundary((k - 0.5) * h, eta, C) != 0.0 ||
+             sigma_boundary((k + 0.5) * h, eta, C) != 0.0;
+    pml[k] = t ? 1 : 0;
+  }
+  if ((st = dalloc(*p, &p->d_inv_s1, n + 2)) || (st = dalloc(*p, &p->d_a1, n + 1)) ||
+      (st = dalloc(*p, &p->d_inv_s2, n + 2)) || (st = dalloc(*p, &p->d_a2, n + 1)) ||
+      (st = dalloc(*p, &p->f_inv_s1, n + 2)) || (st = dalloc(*p, &p->f_a1, n + 1)) ||
+      (st = dalloc(*p, &p->f_inv_s2, n + 2)) || (st = dalloc(*p, &p->f_a2, n + 1)) ||
+      (st = dalloc(*p, &p->d_pml1, n + 2)) || (st = dalloc(*p, &p->d_pml2, n + 2)))
+    return fail(st);
+  cudaMemcpy(p->d_inv_s1, inv_s.data(), (n + 2) * sizeof(c128), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_inv_s2, inv_s.data(), (n + 2) * sizeof(c128), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_a1, a_half.data(), (n + 1) * sizeof(c128), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_a2, a_half.data(), (n + 1) * sizeof(c128), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->f_inv_s1, f_inv_s.data(), (n + 2) * sizeof(c64), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->f_inv_s2, f_inv_s.data(), (n + 2) * sizeof(c64), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->f_a1, f_a_half.data(), (n + 1) * sizeof(c64), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->f_a2, f_a_half.data(), (n + 1) * sizeof(c64), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_pml1, pml.data(), n + 2, cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_pml2, pml.data(), n + 2, cudaMemcpyHostToDevice);
+
+  // ---- per-point omega^2/c^2 and 1/c^2
+  const size_t N2 = (size_t)n * n;
+  {
+    std::vector<double> m0(N2), ci2(N2);
+    std::vector<float> fm0(N2);
+    for (size_t k = 0; k < N2; ++k) {
+      ci2[k] = 1.0 / (c[k] * c[k]);
+      m0[k] = omega * omega * ci2[k];
+      fm0[k] = (float)m0[k];
+    }
+    if ((st = dalloc(*p, &p->d_m0, N2)) || (st = dalloc(*p, &p->f_m0, N2)) || (st = dalloc(*p, &p->d_cinv2, N2)))
+      return fail(st);
+    cudaMemcpy(p->d_m0, m0.data(), N2 * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->f_m0, fm0.data(), N2 * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d_cinv2, ci2.data(), N2 * sizeof(double), cudaMemcpyHostToDevice);
+  }
+
+  // ---- per-block window x2 tables (moving profile of Eq. helma or the
+  //      boundary profile for F and E), and storage offsets
+  std::vector<c128> s2win;
+  // offsets below are counted in complex elements of the factor precision
+  long long fac = 0, red = 0, cor = 0;
+  for (auto& d : p->blocks) {
+    d.s2_off = (int)s2win.size();
+    // x2 absorption of the block's subproblem at coordinate x
+    auto sig = [&](double x) {
+      if (d.kind == BK_F || d.kind == BK_E) return sigma_boundary(x, eta, C);
+      double s = 0.0;
+      if (d.kind == BK_LOWER || d.kind == BK_MIDDLE) s += sigma_moving(x - (d.lo - p->b) * h, eta_b, C);
+      if (d.kind == BK_UPPER || d.kind == BK_MIDDLE) s += sigma_moving((d.hi + p->b) * h - x, eta_b, C);
+      return s;
+    };
+    for (int q = 0; q < d.w; ++q) s2win.push_back(to_c(inv_stretch(sig((d.wlo + q) * h), omega)));
+    for (int q = 0; q < d.w; ++q) s2win.push_back(to_c(stretch(sig((d.wlo + q + 0.5) * h), omega) / (h * h)));
+    for (int q = 0; q < d.w; ++q) s2win.push_back(to_c(stretch(sig((d.wlo + q - 0.5) * h), omega) / (h * h)));
+    d.fac_off = fac; fac += (long long)n * payload_elems(d.W, d.d_out);
+    d.red_off = red; red += (long long)std::max(p->P - 1, 1) * red_elems(d.W);
+    d.cor_off = cor; cor += (long long)p->P * cor_elems(d.W);
+  }
+  p->fac_elems = fac; p->red_elems = red; p->cor_elems = cor;
+  const size_t es = (p->prec == HS_C64) ? sizeof(c64) : sizeof(c128);
+  if ((st = dalloc(*p, &p->d_s2win, s2win.size())) || (st = dalloc(*p, &p->d_blocks, p->blocks.size())) ||
+      (st = dalloc(*p, (char**)&p->d_fac, fac * es)) || (st = dalloc(*p, (char**)&p->d_red, red * es)) ||
+      (st = dalloc(*p, (char**)&p->d_cor, cor * es)) || (st = dalloc(*p, &p->d_status, 4)))
+    return fail(st);
+  cudaMemcpy(p->d_s2win, s2win.data(), s2win.size() * sizeof(c128), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_blocks, p->blocks.data(), p->blocks.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice);
+  cudaMemset(p->d_status, 0, 4 * sizeof(int));
+
+  // ---- sweep workspace for max_nrhs right-hand sides
+  {
+    const size_t R = (size_t)p->max_nrhs;
+    if ((st = dalloc(*p, (char**)&p->d_u, N2 * R * es)) ||
+        (st = dalloc(*p, (char**)&p->d_z, 2 * (size_t)n * R * Wmax * es)) ||
+        (st = dalloc(*p, (char**)&p->d_rc, 2 * (size_t)p->P * R * Wmax * es)) ||
+        (st = dalloc(*p, (char**)&p->d_lc, 2 * (size_t)p->P * R * Wmax * es)) ||
+        (st = dalloc(*p, (char**)&p->d_xs, 2 * (size_t)p->P * R * Wmax * es)) ||
+        (st = dalloc(*p, (char**)&p->d_ps, 2 * (size_t)p->P * R * Wmax * es)))
+      return fail(st);
+  }
+  if (cudaGetLastError() != cudaSuccess) return fail(HS_ECUDA);
+
+  cudaStream_t s = (cudaStream_t)stream;
+  st = launch_setup(*p, s);
+  if (st != HS_OK) return fail(st);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(cuda_status(e));
+  int dst[3];
+  cudaMemcpy(dst, p->d_status, sizeof(dst), cudaMemcpyDeviceToHost);
+  if (dst[0] != HS_OK) return fail(dst[0]);
+  *out = reinterpret_cast<hs_plan*>(p);
+  return HS_OK;
+}

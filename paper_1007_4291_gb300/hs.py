@@ -1,0 +1,163 @@
+"""Thin ctypes binding of libhs (include/hs.h): argument marshalling only.
+
+Every call goes through the C ABI of ``libhs.so``; there is no fallback.  If
+the library is missing or fails to load, ``load()`` raises.  Functions keep
+the C names: ``hs_setup``, ``hs_apply``, ``hs_matvec``, ``hs_solve``,
+``hs_destroy``.  Vector arguments may be torch CUDA tensors (their
+``data_ptr()`` is passed) or raw integer device pointers.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_LIB = None
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libhs.so")
+
+HS_OK, HS_EINVAL, HS_ENOMEM, HS_EBREAKDOWN, HS_ETIMEOUT, HS_ENOCONV, HS_ECUDA, HS_EUNSUPPORTED = range(8)
+HS_C64, HS_C128 = 64, 128
+
+EXPORTED = ["hs_default_options", "hs_setup", "hs_apply", "hs_matvec", "hs_solve", "hs_sync",
+            "hs_last_device_status", "hs_plan_bytes", "hs_destroy", "hs_strerror"]
+
+
+class HsOptions(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("pml_C", ctypes.c_double), ("layers_per_step", ctypes.c_int),
+                ("factor_prec", ctypes.c_int), ("chunk", ctypes.c_int), ("max_nrhs", ctypes.c_int),
+                ("restart", ctypes.c_int), ("reorth", ctypes.c_int), ("spin_budget", ctypes.c_longlong)]
+
+
+class HsSolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("applies", ctypes.c_int),
+                ("max_relres", ctypes.c_double), ("t_apply_ms", ctypes.c_double),
+                ("t_matvec_ms", ctypes.c_double), ("t_orth_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HsError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (status %d)" % (where, strerror(code), code))
+
+
+def load(path=None):
+    """Load libhs.so (raises if it is missing: the CUDA path has no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    p = path or LIBPATH
+    if not os.path.exists(p):
+        raise RuntimeError("libhs.so not built (%s); run paper_1007_4291_gb300.build.build()" % p)
+    lib = ctypes.CDLL(p)
+    vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    lib.hs_default_options.argtypes = [ctypes.POINTER(HsOptions)]
+    lib.hs_setup.argtypes = [vp, d, i, i, i, i, ctypes.POINTER(HsOptions), vp, ctypes.POINTER(vp)]
+    lib.hs_apply.argtypes = [vp, vp, vp, i, i, vp]
+    lib.hs_matvec.argtypes = [vp, vp, vp, i, i, vp]
+    lib.hs_solve.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(HsSolveInfo), vp]
+    lib.hs_sync.argtypes = [vp, vp]
+    lib.hs_last_device_status.argtypes = [vp]
+    lib.hs_plan_bytes.argtypes = [vp]
+    lib.hs_plan_bytes.restype = ll
+    lib.hs_destroy.argtypes = [vp]
+    lib.hs_strerror.argtypes = [i]
+    lib.hs_strerror.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("hs_plan_bytes", "hs_strerror"):
+            getattr(lib, name).restype = i
+    _LIB = lib
+    return lib
+
+
+def strerror(code):
+    if _LIB is None:
+        return "status %d" % code
+    return _LIB.hs_strerror(int(code)).decode()
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("unsupported pointer argument %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream if hasattr(s, "cuda_stream") else int(s)
+
+
+def _check(code, where):
+    if code != HS_OK:
+        raise HsError(code, where)
+    return code
+
+
+def hs_default_options(**kw):
+    lib = load()
+    o = HsOptions()
+    _check(lib.hs_default_options(ctypes.byref(o)), "hs_default_options")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def hs_setup(c, omega, n, dim, pml_width, moving_pml_width, opt=None, stream=None):
+    """Build a plan from host velocities ``c`` (float64, n*n, x1 fastest)."""
+    lib = load()
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    if c.size != n ** dim:
+        raise ValueError("c must hold n**dim values")
+    plan = ctypes.c_void_p()
+    o = opt if opt is not None else hs_default_options()
+    _check(lib.hs_setup(c.ctypes.data, float(omega), int(n), int(dim), int(pml_width), int(moving_pml_width),
+                        ctypes.byref(o), _stream(stream), ctypes.byref(plan)), "hs_setup")
+    return plan
+
+
+def hs_apply(plan, r, z, nrhs, dtype, stream=None):
+    return _check(load().hs_apply(plan, _ptr(r), _ptr(z), int(nrhs), int(dtype), _stream(stream)), "hs_apply")
+
+
+def hs_matvec(plan, x, y, nrhs, dtype, stream=None):
+    return _check(load().hs_matvec(plan, _ptr(x), _ptr(y), int(nrhs), int(dtype), _stream(stream)), "hs_matvec")
+
+
+def hs_solve(plan, f, u, nrhs, tol, maxit, stream=None, check=True):
+    """Returns (status, info dict).  Raises on errors other than HS_ENOCONV
+    unless ``check`` is False."""
+    info = HsSolveInfo()
+    code = load().hs_solve(plan, _ptr(f), _ptr(u), int(nrhs), float(tol), int(maxit), ctypes.byref(info),
+                           _stream(stream))
+    if check and code not in (HS_OK, HS_ENOCONV):
+        raise HsError(code, "hs_solve")
+    return code, info.as_dict()
+
+
+def hs_sync(plan, stream=None):
+    return load().hs_sync(plan, _stream(stream))
+
+
+def hs_last_device_status(plan):
+    return load().hs_last_device_status(plan)
+
+
+def hs_plan_bytes(plan):
+    return load().hs_plan_bytes(plan)
+
+
+def hs_destroy(plan):
+    return load().hs_destroy(plan)
