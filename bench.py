@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the moving-PML sweeping preconditioner on GB300.
+
+One step = the whole hot path on one batch: hs_setup (batched factorisation
+of every moving-PML subproblem) + hs_solve (FGMRES to relative residual
+1e-6 with the two-front sweep as preconditioner, FP64 matvec and
+Gram-Schmidt) for 64 right-hand sides on the 2D n = 2047 grid
+(omega/2pi = 128, 16 points per wavelength), synthetic seeded inputs.
+
+Prints one JSON line (rank 0).  `value` = right-hand sides solved to 1e-6
+per second (whole job, all GPUs), with f resident on the device; `e2e` is the
+same through the C ABI with host buffers (f copied in, u copied out, c read
+from host by hs_setup) inside the timed region.  `--impl reference` times the
+complex128 CPU oracle on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GMRES time-to-1e-6 & sweep applies/s (2D n=2047, 64 RHS), % HBM roofline"
+UNIT = "rhs_solved_per_s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=2047)
+    ap.add_argument("--nrhs", type=int, default=64)
+    ap.add_argument("--dl", type=int, default=12)
+    ap.add_argument("--prec", type=int, default=64, choices=[64, 128])
+    ap.add_argument("--restart", type=int, default=20)
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1007_4291_gb300 import inputs as I
+    n = args.n
+    bp = b = 12
+    freq = (n + 1) / 16.0          # 16 points per wavelength at c = 1
+    c = I.random_velocity(n, 0)    # smooth random field in [0.8, 1.2]
+    f = I.point_sources(n, args.nrhs, 1, bp)
+    return dict(n=n, bp=bp, b=b, omega=2 * np.pi * freq, freq=freq, alpha=2.0, C=20.0, c=c, f=f)
+
+
+def config_dict(args, wl):
+    return {
+        "workload": "2D Helmholtz n=%d (omega/2pi=%g, 16 pts/wavelength), smooth random velocity in [0.8,1.2] "
+                    "(seed 0), %d Gaussian point sources (seed 1), PML 12, moving PML 12, alpha 2, d=%d, "
+                    "complex%d factors, FGMRES(%d) to %.0e" % (wl["n"], wl["freq"], args.nrhs, args.dl,
+                                                             args.prec, args.restart, args.tol),
+        "n": wl["n"], "nrhs": args.nrhs, "omega_over_2pi": wl["freq"], "pml_width": wl["bp"],
+        "moving_pml_width": wl["b"], "layers_per_step": args.dl, "factor_prec": "c%d" % args.prec,
+        "restart": args.restart, "tol": args.tol,
+        "l2": "inputs larger than L2 (f is %.1f GB, factors and Krylov basis tens of GB)" %
+              (wl["f"].nbytes / 1e9),
+        "step": "hs_setup + hs_solve (+ hs_destroy)",
+    }
+
+
+# ----------------------------------------------------------------------------- accounting
+def blocks(n, bp, b, dL):
+    """Window heights of the two-front partition (F, lower blocks, middle, and
+    mirrors): list of (w, uses per apply)."""
+    rows_front = (n - 1) // 2 - bp
+    sizes = [dL] * (rows_front // dL) + ([rows_front % dL] if rows_front % dL else [])
+    out = [(bp, 2), (bp, 2)]
+    for d in sizes:
+        out += [(d + b - 1, 2), (d + b - 1, 2)]
+    out.append((2 * b - 1, 1))
+    return out
+
+
+def sweep_flops(n, bp, b, dL, R):
+    """Algorithmic flops of one application of M_alpha to R RHS: every T~_B
+    solve costs 2 w^2 n complex multiply-adds (forward and back substitution
+    of the band factor), 8 real flops each; two solves per block per apply
+    (forward and backward sweep), one for the middle layer."""
+    return sum(u * 2 * w * w * n * 8 for w, u in blocks(n, bp, b, dL)) * R
+
+
+def sweep_bytes(n, bp, b, dL, R, es=8):
+    """Algorithmic DRAM bytes of one application (c64): symmetric factor of
+    every block read once per solve (w(w+1)/2 entries per column) plus four
+    passes over the R-RHS vector."""
+    fac = sum(u * n * (w * (w + 1) // 2) * es for w, u in blocks(n, bp, b, dL))
+    return fac + 4 * n * n * R * es
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle leg
+def oracle_sample(wl, nrhs, iters, budget_s=20.0):
+    """Time the complex128 oracle on a bounded sample of the workload and
+    extrapolate a 64-RHS solve: factor k blocks and apply their T~ to all RHS,
+    one sparse matvec, then scale by the block count and iteration count."""
+    from oracle import helmholtz2d as H
+    from oracle import sweep2d as S
+    n, bp, b, dL = wl["n"], wl["bp"], wl["b"], 12
+    lower, upper, mid = S.partition(n, bp, b, dL)
+    allb = lower + upper + [mid]
+    r = np.ascontiguousarray(wl["f"][:nrhs])
+    t_fac, t_sol, k = 0.0, 0.0, 0
+    t0 = time.perf_counter()
+    for blk in lower[1:]:
+        ta = time.perf_counter()
+        fb = S.factor_block(blk, wl["c"], wl["omega"], bp, b, wl["C"], wl["alpha"])
+        tb = time.perf_counter()
+        fb.t_tilde(r[:, blk.lo - 1:blk.hi, :])
+        tc = time.perf_counter()
+        t_fac += tb - ta
+        t_sol += tc - tb
+        k += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    ta = time.perf_counter()
+    A = H.helmholtz_matrix(wl["c"], wl["omega"], bp, wl["C"], 0.0)
+    x = r.reshape(nrhs, -1).T
+    _ = A @ x
+    t_mv = time.perf_counter() - ta
+    nblk = len(allb)
+    solves_per_apply = 2 * (nblk - 1) + 1
+    t_setup = t_fac / k * nblk
+    t_apply = t_sol / k * solves_per_apply
+    t_total = t_setup + iters * (t_apply + t_mv)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {
+        "value": nrhs / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "threads_used": "NumPy/SciPy LAPACK defaults (zgbtrf/zgbtrs, sparse matvec)",
+        "sample": "n=%d: factored %d of %d moving-PML blocks (zgbtrf) and applied T~ to %d RHS (zgbtrs), "
+                  "one sparse FP64 matvec; time-to-1e-6 extrapolated as setup + %d x (apply + matvec), "
+                  "Gram-Schmidt not counted; %.1f s of CPU work" % (n, k, nblk, nrhs, iters,
+                                                                    time.perf_counter() - t0),
+        "t_extrapolated_s": t_total,
+    }
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(args)
+    iters = 12
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(wl, args.nrhs, iters, budget_s=5.0)
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = oracle_sample(wl, args.nrhs, iters, budget_s=10.0)
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    v = statistics.median(vals)
+    cb = dict(last)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": config_dict(args, wl), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU leg
+def run_ours(args):
+    import torch
+    import __graft_entry__ as G
+    from paper_1007_4291_gb300 import hs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    G.build()
+    lib = hs.load()
+    wl = workload(args)
+    n, R = wl["n"], args.nrhs
+    opt = hs.hs_default_options(alpha=wl["alpha"], pml_C=wl["C"], layers_per_step=args.dl, factor_prec=args.prec,
+                                chunk=args.chunk, max_nrhs=R, restart=args.restart)
+    stream = torch.cuda.current_stream()
+    c_host = np.ascontiguousarray(wl["c"].ravel())
+    f_dev = torch.from_numpy(wl["f"]).to("cuda")
+    u_dev = torch.zeros_like(f_dev)
+
+    def step():
+        plan = hs.hs_setup(c_host, wl["omega"], n, 2, wl["bp"], wl["b"], opt, stream)
+        u_dev.zero_()
+        code, info = hs.hs_solve(plan, f_dev, u_dev, R, args.tol, 400, stream)
+        hs.hs_destroy(plan)
+        if code != hs.HS_OK:
+            raise RuntimeError("hs_solve did not converge: %s" % info)
+        return info
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(local)
+    l0 = lib.hs_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(stream)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        infos.append(step())
+    e1.record(stream)
+    barrier()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    launches = lib.hs_kernel_launches() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_all = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    value = world * R / (ms_all / 1e3)
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        f_host = torch.from_numpy(wl["f"]).pin_memory()
+        u_host = torch.empty_like(f_host).pin_memory()
+
+        def step_e2e():
+            f_dev.copy_(f_host, non_blocking=True)
+            plan = hs.hs_setup(c_host, wl["omega"], n, 2, wl["bp"], wl["b"], opt, stream)
+            u_dev.zero_()
+            code, info = hs.hs_solve(plan, f_dev, u_dev, R, args.tol, 400, stream)
+            hs.hs_destroy(plan)
+            u_host.copy_(u_dev, non_blocking=True)
+            return code
+
+        step_e2e()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_e2e()
+        barrier()
+        we = (time.perf_counter() - t0) / args.steps
+        if dist is not None:
+            t = torch.tensor([we], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            we = float(t.item())
+        e2e = {"value": world * R / we, "unit": UNIT, "h2d_bytes_per_step": int(wl["f"].nbytes + c_host.nbytes),
+               "d2h_bytes_per_step": int(wl["f"].nbytes), "ms_per_step": we * 1e3}
+
+    # roofline of the dominant kernel: the sweep application (FP32 ALU bound at 64 RHS)
+    applies = sum(i["applies"] for i in infos)
+    t_apply = sum(i["t_apply_ms"] for i in infos) / 1e3
+    fl = sweep_flops(n, wl["bp"], wl["b"], args.dl, R)
+    by = sweep_bytes(n, wl["bp"], wl["b"], args.dl, R)
+    per_apply = t_apply / max(applies, 1)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s at the maximum SM clock
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = fl / per_apply / 1e12
+    roofline = {"bound": "alu", "kernel": "sweep application M_alpha (phase 1/2/3 kernels of all stages)",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock of measured)" % sm_max,
+                "traffic": None,
+                "hbm_achieved_gbs": by / per_apply / 1e9, "hbm_peak_gbs": hbm,
+                "hbm_frac": by / per_apply / 1e9 / hbm,
+                "algorithmic_flops_per_apply": fl, "algorithmic_bytes_per_apply": by,
+                "ms_per_apply": per_apply * 1e3}
+    it = [i["iterations"] for i in infos]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c%d" % args.prec, "data": "synthetic", "config": config_dict(args, wl),
+        "time_to_1e6_s": ms_all / 1e3,
+        "sweep": {"rhs_applies_per_s": R * applies / t_apply if t_apply > 0 else None,
+                  "applies_per_step": applies / args.steps},
+        "solve": {"iterations": it, "max_relres": max(i["max_relres"] for i in infos),
+                  "t_apply_ms": statistics.mean(i["t_apply_ms"] for i in infos),
+                  "t_matvec_ms": statistics.mean(i["t_matvec_ms"] for i in infos),
+                  "t_orth_ms": statistics.mean(i["t_orth_ms"] for i in infos),
+                  "t_solve_ms": statistics.mean(i["t_total_ms"] for i in infos)},
+        "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches),
+        "gpu_launches_per_step": launches / args.steps, "wall_s_timed": wall,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = oracle_sample(wl, R, max(it))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

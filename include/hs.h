@@ -134,8 +134,20 @@ int hs_sync(hs_plan* plan, void* stream);
 /* Status recorded by device kernels since setup (HS_OK if none). */
 int hs_last_device_status(hs_plan* plan);
 
-/* Bytes of device memory owned by the plan. */
+/* Bytes of device memory owned by the plan (factors, tables, sweep workspace). */
 long long hs_plan_bytes(const hs_plan* plan);
+
+/*
+ * hs_solve draws its Krylov basis (restart+1 FP64 vectors and restart
+ * preconditioned vectors of nrhs RHS) from one device buffer shared by the
+ * whole process; it grows on demand and is kept between calls so that
+ * repeated solves do not reallocate.  Solves from several host threads take
+ * turns on it.  hs_release_workspace() frees it (no solve may be running).
+ */
+int hs_release_workspace(void);
+
+/* Diagnostic: number of kernels libhs has launched in this process. */
+long long hs_kernel_launches(void);
 
 /* Free the plan and all device memory it owns.  NULL is accepted. */
 int hs_destroy(hs_plan* plan);

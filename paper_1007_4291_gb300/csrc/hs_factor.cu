@@ -386,10 +386,12 @@ int launch_w(Plan& p, FactorArgs a, const std::vector<int>& ids, cudaStream_t s)
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // One persistent launch over all (block, chunk) work items of this width.
   int grid = std::min<long long>(a.nitems, (long long)sms * 16);
+  note_launch();
   factor_chunks_kernel<R, W><<<grid, 32, smem, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && p.P > 1) {
     int g2 = std::min(a.nblocks, sms * 16);
+    note_launch();
     factor_reduced_kernel<R, W><<<g2, 32, smem, s>>>(a);
     e = cudaGetLastError();
   }

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <vector>
 #include <string>
+#include <atomic>
 #include "../../include/hs.h"
 
 namespace hs {
@@ -100,8 +101,8 @@ struct Plan {
   void* d_ps = nullptr;     // separator forward values psi
   int* d_status = nullptr;  // device status word(s): [0] code, [1] block, [2] column
   long long bytes = 0;
-  // Krylov workspace (allocated on first hs_solve)
-  c128* d_V = nullptr; c64* d_Zk = nullptr; c128* d_w = nullptr; c128* d_x = nullptr; c128* d_f = nullptr;
+  // Krylov workspace, carved from the process-wide pool for the duration of hs_solve
+  c128* d_V = nullptr; c64* d_Zk = nullptr; c128* d_x = nullptr; c128* d_f = nullptr;
   c128* d_part = nullptr; c128* d_h = nullptr; double* d_nrm = nullptr;
   int kry_m = 0, kry_R = 0;
   long long kry_bytes = 0;
@@ -109,6 +110,9 @@ struct Plan {
 
 // ---------------------------------------------------------------- helpers
 int cuda_status(cudaError_t e);
+// Number of kernels libhs has launched in this process (all streams).
+extern std::atomic<long long> g_launches;
+inline void note_launch(long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 #define HS_CUDA_TRY(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) return hs::cuda_status(_e); } while (0)
 
 int padded_width(int w);   // 8, 12, 16, 24, 32 or -1

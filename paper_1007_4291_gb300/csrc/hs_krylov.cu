@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <mutex>
 #include <vector>
 #include "hs_internal.cuh"
 
@@ -165,32 +166,40 @@ struct Kry {
   // h[i][r] (i < nv) and |w|^2 (slot nv) into p.d_h
   void dots(const c128* V, int nv, const c128* w) {
     const dim3 g = grid();
+    note_launch();
     if (nv <= 8) dots_kernel<8><<<g, KT, 0, s>>>(V, vstride, nv, w, npts, R, p.d_part);
     else if (nv <= 16) dots_kernel<16><<<g, KT, 0, s>>>(V, vstride, nv, w, npts, R, p.d_part);
     else dots_kernel<32><<<g, KT, 0, s>>>(V, vstride, nv, w, npts, R, p.d_part);
     const int mj = (nv <= 8) ? 8 : (nv <= 16) ? 16 : 32;
     const int tot = (nv + 1) * R;
+    note_launch();
     reduce_parts_kernel<<<(tot + 255) / 256, 256, 0, s>>>(p.d_part, nctas, mj + 1, nv + 1, R, p.d_h);
   }
   // w -= V h ; |w|^2 -> p.d_h row `slot`
   void update(const c128* V, int nv, const c128* h, c128* w, int slot) {
     const dim3 g = grid();
+    note_launch();
     if (nv <= 8) update_kernel<8><<<g, KT, 0, s>>>(V, vstride, nv, h, w, npts, R, p.d_part);
     else if (nv <= 16) update_kernel<16><<<g, KT, 0, s>>>(V, vstride, nv, h, w, npts, R, p.d_part);
     else update_kernel<32><<<g, KT, 0, s>>>(V, vstride, nv, h, w, npts, R, p.d_part);
+    note_launch();
     reduce_parts_kernel<<<(R + 255) / 256, 256, 0, s>>>(p.d_part, nctas, 1, 1, R, p.d_h + (long long)slot * R);
   }
   void norm2(const c128* w, int slot) {
+    note_launch();
     dots_kernel<8><<<grid(), KT, 0, s>>>(nullptr, vstride, 0, w, npts, R, p.d_part);
+    note_launch();
     reduce_parts_kernel<<<(R + 255) / 256, 256, 0, s>>>(p.d_part, nctas, 9, 1, R, p.d_h + (long long)slot * R);
   }
   void scale(const c128* w, const std::vector<double>& f, c128* v) {
     cudaMemcpyAsync(p.d_nrm, f.data(), R * sizeof(double), cudaMemcpyHostToDevice, s);
+    note_launch();
     scale_kernel<<<sm_count() * 8, 256, 0, s>>>(w, p.d_nrm, v, npts * R, R);
   }
   template <typename ZT>
   void xupdate(const cplx<ZT>* Z, int k, const c128* y, c128* x) {
     const dim3 g = grid();
+    note_launch();
     if (k <= 8) xupdate_kernel<8, ZT><<<g, KT, 0, s>>>(Z, vstride, k, y, x, npts, R);
     else if (k <= 16) xupdate_kernel<16, ZT><<<g, KT, 0, s>>>(Z, vstride, k, y, x, npts, R);
     else xupdate_kernel<32, ZT><<<g, KT, 0, s>>>(Z, vstride, k, y, x, npts, R);
@@ -207,27 +216,51 @@ void givens(zc a, zc b, double& c, zc& s) {
   s = (a / std::abs(a)) * std::conj(b) / na;
 }
 
-int ensure_workspace(Plan& p, int m, int R) {
-  if (p.d_V && p.kry_m >= m && p.kry_R >= R) return HS_OK;
+// Process-wide Krylov workspace: one device allocation reused by every
+// hs_solve (held under a mutex for the duration of a solve, so concurrent
+// solves from several host threads serialise instead of racing).  It grows
+// when a solve needs more and is returned by hs_release_workspace().
+struct KrylovPool {
+  std::mutex mu;
+  char* base = nullptr;
+  size_t bytes = 0;
+};
+KrylovPool& pool() {
+  static KrylovPool kp;
+  return kp;
+}
+
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+int carve_workspace(Plan& p, int m, int R) {
+  KrylovPool& kp = pool();
   const size_t zes = (p.prec == HS_C64) ? sizeof(c64) : sizeof(c128);
-  for (void* q : {(void*)p.d_V, (void*)p.d_Zk, (void*)p.d_x, (void*)p.d_f, (void*)p.d_part, (void*)p.d_h,
-                  (void*)p.d_nrm})
-    if (q) cudaFree(q);
-  p.d_V = nullptr; p.d_Zk = nullptr; p.d_x = nullptr; p.d_f = nullptr; p.d_part = nullptr; p.d_h = nullptr;
-  p.d_nrm = nullptr; p.kry_bytes = 0;
   const size_t npts = (size_t)p.n * p.n, vs = npts * R;
   const size_t nct = (size_t)sm_count() * 2;
-  size_t b1 = (m + 1) * vs * sizeof(c128), b2 = m * vs * zes, b3 = vs * sizeof(c128);
-  size_t b4 = nct * 33 * R * sizeof(c128), b5 = 34 * R * sizeof(c128);
-  if (cudaMalloc(&p.d_V, b1) != cudaSuccess || cudaMalloc(&p.d_Zk, b2) != cudaSuccess ||
-      cudaMalloc(&p.d_x, b3) != cudaSuccess || cudaMalloc(&p.d_f, b3) != cudaSuccess ||
-      cudaMalloc(&p.d_part, b4) != cudaSuccess || cudaMalloc(&p.d_h, b5) != cudaSuccess ||
-      cudaMalloc(&p.d_nrm, R * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    return HS_ENOMEM;
+  const size_t b1 = al256((m + 1) * vs * sizeof(c128)), b2 = al256(m * vs * zes), b3 = al256(vs * sizeof(c128));
+  const size_t b4 = al256(nct * 33 * R * sizeof(c128)), b5 = al256(34 * R * sizeof(c128)), b6 = al256(R * sizeof(double));
+  const size_t need = b1 + b2 + 2 * b3 + b4 + b5 + b6;
+  if (kp.bytes < need) {
+    if (kp.base) cudaFree(kp.base);
+    kp.base = nullptr;
+    kp.bytes = 0;
+    if (cudaMalloc(&kp.base, need) != cudaSuccess) {
+      cudaGetLastError();
+      kp.base = nullptr;
+      return HS_ENOMEM;
+    }
+    kp.bytes = need;
   }
+  char* q = kp.base;
+  p.d_V = (c128*)q; q += b1;
+  p.d_Zk = (c64*)q; q += b2;
+  p.d_x = (c128*)q; q += b3;
+  p.d_f = (c128*)q; q += b3;
+  p.d_part = (c128*)q; q += b4;
+  p.d_h = (c128*)q; q += b5;
+  p.d_nrm = (double*)q;
   p.kry_m = m; p.kry_R = R;
-  p.kry_bytes = (long long)(b1 + b2 + 2 * b3 + b4 + b5 + R * sizeof(double));
+  p.kry_bytes = (long long)need;
   return HS_OK;
 }
 
@@ -245,7 +278,8 @@ extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double 
   cudaStream_t s = (cudaStream_t)stream;
   const int R = nrhs;
   const int m = std::min(std::max(p.opt.restart, 1), 32);
-  int st = ensure_workspace(p, m, R);
+  std::lock_guard<std::mutex> guard(pool().mu);
+  int st = carve_workspace(p, m, R);
   if (st != HS_OK) return st;
   const long long npts = (long long)p.n * p.n, vs = npts * R;
   Kry K{p, R, npts, vs, s, sm_count() * 2};
@@ -306,6 +340,7 @@ extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double 
       // z_j = M_alpha v_j in the factor precision, computed in place in Z_j
       cudaEventRecord(ev[0], s);
       if (p.prec == HS_C64) {
+        note_launch();
         to_c64_kernel<<<sm_count() * 8, 256, 0, s>>>(Vj, Zj, vs);
         p.d_u = Zj;
       } else {
@@ -418,4 +453,13 @@ extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double 
   }
   if (st == HS_OK && (mx > tol || nan)) st = HS_ENOCONV;
   return st;
+}
+
+extern "C" int hs_release_workspace(void) {
+  KrylovPool& kp = pool();
+  std::lock_guard<std::mutex> guard(kp.mu);
+  if (kp.base) cudaFree(kp.base);
+  kp.base = nullptr;
+  kp.bytes = 0;
+  return HS_OK;
 }

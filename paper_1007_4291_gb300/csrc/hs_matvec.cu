@@ -91,9 +91,11 @@ int grid_for(long long total) {
 int matvec_abi(Plan& p, const void* x, void* y, int nrhs, int dtype, cudaStream_t s) {
   const long long total = (long long)p.n * p.n * nrhs;
   if (dtype == HS_C128) {
+    note_launch();
     matvec_kernel<double, double, double, false, false><<<grid_for(total), 256, 0, s>>>(
         (const c128*)x, (c128*)y, nullptr, tabs<double>(p), p.n, nrhs);
   } else {
+    note_launch();
     matvec_kernel<float, float, float, false, false><<<grid_for(total), 256, 0, s>>>(
         (const c64*)x, (c64*)y, nullptr, tabs<float>(p), p.n, nrhs);
   }
@@ -104,6 +106,7 @@ int matvec_abi(Plan& p, const void* x, void* y, int nrhs, int dtype, cudaStream_
 int matvec_internal_f64(Plan& p, const void* x, bool x_is_c64, c128* y, const c128* f, int R, cudaStream_t s) {
   const long long total = (long long)p.n * p.n * R;
   const int g = grid_for(total);
+  note_launch();
   if (x_is_c64) {
     if (f) matvec_kernel<float, double, double, true, true><<<g, 256, 0, s>>>((const c64*)x, y, f, tabs<double>(p), p.n, R);
     else matvec_kernel<float, double, double, true, false><<<g, 256, 0, s>>>((const c64*)x, y, f, tabs<double>(p), p.n, R);

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <algorithm>
 #include <complex>
+#include <atomic>
 #include "hs_internal.cuh"
 #include "hs_device.cuh"
 
@@ -135,7 +136,7 @@ static void free_plan_memory(Plan* p) {
   void* ptrs[] = {p->d_inv_s1, p->d_a1, p->d_inv_s2, p->d_a2, p->f_inv_s1, p->f_a1, p->f_inv_s2, p->f_a2,
                   p->d_pml1, p->d_pml2, p->d_m0, p->f_m0, p->d_cinv2, p->d_s2win, p->d_blocks,
                   p->d_fac, p->d_red, p->d_cor, p->d_u, p->d_z, p->d_rc, p->d_lc, p->d_xs, p->d_ps,
-                  p->d_status, p->d_V, p->d_Zk, p->d_w, p->d_x, p->d_f, p->d_part, p->d_h, p->d_nrm};
+                  p->d_status};
   for (void* q : ptrs) if (q) cudaFree(q);
 }
 
@@ -151,8 +152,12 @@ extern "C" int hs_destroy(hs_plan* plan) {
 extern "C" long long hs_plan_bytes(const hs_plan* plan) {
   if (!plan) return 0;
   const Plan* p = reinterpret_cast<const Plan*>(plan);
-  return p->bytes + p->kry_bytes;
+  return p->bytes;
 }
+
+std::atomic<long long> hs::g_launches{0};
+
+extern "C" long long hs_kernel_launches(void) { return hs::g_launches.load(); }
 
 extern "C" int hs_last_device_status(hs_plan* plan) {
   if (!plan) return HS_EINVAL;

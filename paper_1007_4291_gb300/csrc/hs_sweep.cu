@@ -484,12 +484,15 @@ int run_stage_w(const Plan& p, SweepArgs a, cudaStream_t s) {
     attr_set = true;
   }
   dim3 g13(a.P, (a.R + RT - 1) / RT, a.nfront);
+  note_launch();
   phase1_kernel<R, W, T><<<g13, NT, sm13, s>>>(a);
   if (a.P > 1) {
     const size_t sm2 = 128 + 2 * (((size_t)red_elems(W) * sizeof(cplx<R>) + 127) / 128 * 128);
     dim3 g2(1, (a.R + NT / 32 - 1) / (NT / 32), a.nfront);
+    note_launch();
     phase2_kernel<R, W><<<g2, NT, sm2, s>>>(a);
   }
+  note_launch();
   phase3_kernel<R, W, T><<<g13, NT, sm13, s>>>(a);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HS_OK : cuda_status(e);
@@ -577,6 +580,7 @@ __global__ void relayout_kernel(const cplx<Ti>* __restrict__ src, cplx<To>* __re
 template <typename Ti, typename To, bool TI>
 int relayout(const void* src, void* dst, long long npts, int R, cudaStream_t s) {
   dim3 grid((unsigned)((npts + 31) / 32), (R + 31) / 32);
+  note_launch();
   relayout_kernel<Ti, To, TI><<<grid, dim3(32, 8), 0, s>>>(reinterpret_cast<const cplx<Ti>*>(src),
                                                            reinterpret_cast<cplx<To>*>(dst), npts, R);
   cudaError_t e = cudaGetLastError();
