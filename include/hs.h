@@ -107,6 +107,31 @@ int hs_setup(const double* c, double omega, int n, int dim, int pml_width, int m
 int hs_apply(hs_plan* plan, const void* r, void* z, int nrhs, int dtype, void* stream);
 
 /*
+ * hs_apply_noalloc -- z = M_alpha r like hs_apply, for callers that must not
+ * allocate device memory when they apply the preconditioner (applications
+ * that hand all free device memory to their own pool at start-up,
+ * latency-critical loops that cannot afford cudaMalloc's implicit device
+ * synchronisation, hosts that forbid a library from allocating after
+ * initialisation).  The paper has no counterpart; this is a deployment
+ * variant of the same sweep.
+ *
+ * It allocates nothing: all temporaries (working vector, chunk store,
+ * separator buffers) live in one file-scope device array of 32 MiB that every
+ * device loading the library holds until the process exits; the plan's own
+ * workspace is not used.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Calls share the array and it keeps
+ * the last call's contents (nothing in it needs to start at zero), so calls
+ * that overlap on the GPU race: serialise them.  Returns HS_EINVAL when the
+ * problem does not fit: n*n*nrhs + 2*n*nrhs*Wmax + 8*P*nrhs*Wmax elements of
+ * the factor precision (Wmax <= 32 the padded window height, P the number of
+ * x1 chunks), each rounded up to 256 bytes, must not exceed 32 MiB (for
+ * example n = 511 with up to 14 right-hand sides in complex64).
+ * Arguments as hs_apply.
+ */
+int hs_apply_noalloc(hs_plan* plan, const void* r, void* z, int nrhs, int dtype, void* stream);
+
+/*
  * hs_matvec -- y = A x with the Eq. helmd operator (alpha = 0).
  * dtype HS_C128 computes in FP64, HS_C64 in FP32.  x and y must not alias.
  */

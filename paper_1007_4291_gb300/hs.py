@@ -57,6 +57,8 @@ def load(path=None):
     lib.hs_setup.argtypes = [vp, d, i, i, i, i, ctypes.POINTER(HsOptions), vp, ctypes.POINTER(vp)]
     lib.hs_apply.argtypes = [vp, vp, vp, i, i, vp]
     lib.hs_matvec.argtypes = [vp, vp, vp, i, i, vp]
+    lib.hs_apply_noalloc.argtypes = [vp, vp, vp, i, i, vp]
+    lib.hs_apply_noalloc.restype = i
     lib.hs_solve.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(HsSolveInfo), vp]
     lib.hs_sync.argtypes = [vp, vp]
     lib.hs_last_device_status.argtypes = [vp]
@@ -130,6 +132,12 @@ def hs_setup(c, omega, n, dim, pml_width, moving_pml_width, opt=None, stream=Non
 
 def hs_apply(plan, r, z, nrhs, dtype, stream=None):
     return _check(load().hs_apply(plan, _ptr(r), _ptr(z), int(nrhs), int(dtype), _stream(stream)), "hs_apply")
+
+
+def hs_apply_noalloc(plan, r, z, nrhs, dtype, stream=None):
+    """hs_apply with all temporaries in the library's static device scratch."""
+    return _check(load().hs_apply_noalloc(plan, _ptr(r), _ptr(z), int(nrhs), int(dtype), _stream(stream)),
+                  "hs_apply_noalloc")
 
 
 def hs_matvec(plan, x, y, nrhs, dtype, stream=None):
