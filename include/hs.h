@@ -52,10 +52,10 @@ typedef struct {
   double pml_C;          /* C of Eq. sigma (PML strength, same for boundary and moving PMLs).         default 20 */
   int layers_per_step;   /* d of Sec. 2.3 (rows eliminated per sweep step).                           default 12 */
   int factor_prec;       /* HS_C64: complex float factors and sweep; HS_C128: complex double.          default HS_C64 */
-  int chunk;             /* x1 columns per partition chunk of the subproblem solves (>= 2; 0 = auto). default 0 */
+  int chunk;             /* x1 columns per partition chunk (>= 2; raised to ceil(n/65); 0 = 32).     default 0 */
   int max_nrhs;          /* largest nrhs any later call will use (workspace is sized at setup).       default 64 */
   int restart;           /* FGMRES restart length m.                                                  default 20 */
-  int reorth;            /* 0: classical Gram-Schmidt; 1: CGS with a second pass when needed (DGKS).  default 1 */
+  int reorth;            /* 0: classical Gram-Schmidt; 1: CGS with a second pass when needed (DGKS).  default 0 */
   long long spin_budget; /* SM clock cycles a device-side barrier wait may take before HS_ETIMEOUT.   default 1<<30 */
 } hs_options;
 

@@ -31,6 +31,11 @@ __device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_
       : "memory");
 }
 
+// Plain arrive (no transaction bytes): consumer release of a ring stage.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -43,10 +48,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for phase `parity` of `bar` for at most `budget` clock cycles.
+// Non-blocking probe of phase `parity` of `bar`.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of `bar` for at most `budget` clock cycles,
+// polling with the non-blocking probe (no suspension of the warp).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long budget) {
-  long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_test_wait(bar, parity)) {
     if (clock64() - t0 > budget) return false;
   }
   return true;
@@ -92,16 +112,21 @@ template <typename R> __device__ __forceinline__ cplx<R> shfl_xor_c(cplx<R> v, i
   return cplx<R>{Shfl<R>::xr(v.re, m, width), Shfl<R>::xr(v.im, m, width)};
 }
 
+// Row stride (complex elements) of the factor payloads in global memory: W+2
+// keeps every row 16-byte aligned (128-bit shared-memory loads) and the rows
+// read by the T row-slices of the sweep in distinct banks.
+__host__ __device__ __forceinline__ int payload_ld(int W) { return W + 2; }
+
 // Number of complex elements of one column payload of a block's factor:
-// G (W x (W+1), padded rows), V (d_out x (W+1)), c (W), rounded up to an even
-// count so that every payload is a multiple of 16 bytes.
+// G (W x (W+2)), V (d_out x (W+2)), c (W), rounded up to an even count so
+// that every payload is a multiple of 16 bytes.
 __host__ __device__ __forceinline__ long long payload_elems(int W, int d_out) {
-  long long e = (long long)(W + d_out) * (W + 1) + W;
+  long long e = (long long)(W + d_out) * payload_ld(W) + W;
   return (e + 1) & ~1LL;
 }
-// Reduced-system factors per separator: Gamma and F, each W x (W+1).
-__host__ __device__ __forceinline__ long long red_elems(int W) { return 2LL * W * (W + 1); }
-// Corner blocks per interior chunk: G_r, W_l, W_r, each W x (W+1).
+// Reduced-system factors per separator: Gamma and F, each W x (W+2).
+__host__ __device__ __forceinline__ long long red_elems(int W) { return 2LL * W * payload_ld(W); }
+// Corner blocks per interior chunk: G_r, W_l, W_r, each W x (W+1) (setup only).
 __host__ __device__ __forceinline__ long long cor_elems(int W) { return 3LL * W * (W + 1); }
 
 }  // namespace hs

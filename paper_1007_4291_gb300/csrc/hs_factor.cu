@@ -161,19 +161,22 @@ __device__ bool invert_inplace(cplx<R>* A, int* piv, int lane) {
   return __all_sync(0xffffffffu, ok);
 }
 
+// Copy rows row0 .. row0+nrows-1 of a shared W x (W+1) matrix to global
+// memory with row stride `ld` (payload_ld(W) for payloads, W+1 for corners).
 template <typename R, int W>
-__device__ __forceinline__ void store_rows(cplx<R>* dst, const cplx<R>* src, int lane, int row0, int nrows) {
+__device__ __forceinline__ void store_rows(cplx<R>* dst, const cplx<R>* src, int lane, int row0, int nrows, int ld) {
   constexpr int LD = W + 1;
   if (lane >= row0 && lane < row0 + nrows) {
 #pragma unroll 4
-    for (int q = 0; q < LD; ++q) dst[(lane - row0) * LD + q] = src[lane * LD + q];
+    for (int q = 0; q < W; ++q) dst[(lane - row0) * ld + q] = src[lane * LD + q];
   }
 }
 
 template <typename R, int W>
 __global__ void __launch_bounds__(32) factor_chunks_kernel(FactorArgs a) {
   using C = cplx<R>;
-  constexpr int LD = W + 1;
+  constexpr int LD = W + 1;          // shared work matrices
+  constexpr int LDP = W + 2;         // global payload rows (payload_ld)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* bufA = reinterpret_cast<C*>(smem_raw);
   C* bufG = bufA + W * LD;
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(32) factor_chunks_kernel(FactorArgs a) {
           sub_cgc<R, W>(A, G, cv, lane);
         }
         ok &= invert_inplace<R, W>(A, piv, lane);
-        store_rows<R, W>(fac + (long long)j * pe, A, lane, 0, W);
+        store_rows<R, W>(fac + (long long)j * pe, A, lane, 0, W, LDP);
         C* t = A; A = G; G = t;
         __syncwarp();
       }
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(32) factor_chunks_kernel(FactorArgs a) {
       if (has_left) {
         if (lane < W) {
 #pragma unroll 4
-          for (int q = 0; q < W; ++q) Tm[lane * LD + q] = slot[lane * LD + q];
+          for (int q = 0; q < W; ++q) Tm[lane * LD + q] = slot[lane * LDP + q];
         }
         __syncwarp();
         if (j > l) {
@@ -247,25 +250,25 @@ __global__ void __launch_bounds__(32) factor_chunks_kernel(FactorArgs a) {
           __syncwarp();
         }
         C* t = Wsp; Wsp = Tm; Tm = t;    // Wsp = W_j
-        store_rows<R, W>(slot + (long long)W * LD, Wsp, lane, d.out_off, d.d_out);
-        if (j == l) store_rows<R, W>(cor + (long long)W * LD, Wsp, lane, 0, W);
-        if (j == r) store_rows<R, W>(cor + 2LL * W * LD, Wsp, lane, 0, W);
+        store_rows<R, W>(slot + (long long)W * LDP, Wsp, lane, d.out_off, d.d_out, LDP);
+        if (j == l) store_rows<R, W>(cor + (long long)W * LD, Wsp, lane, 0, W, LD);
+        if (j == r) store_rows<R, W>(cor + 2LL * W * LD, Wsp, lane, 0, W, LD);
         __syncwarp();
       }
       build_d<R, W>(a, d, s2, j, A, lane);
       if (j > l) sub_cgc<R, W>(A, G, cv + W, lane);
       ok &= invert_inplace<R, W>(A, piv, lane);
-      store_rows<R, W>(slot, A, lane, 0, W);
-      if (j == r) store_rows<R, W>(cor, A, lane, 0, W);
+      store_rows<R, W>(slot, A, lane, 0, W, LDP);
+      if (j == r) store_rows<R, W>(cor, A, lane, 0, W, LD);
       C* t = A; A = G; G = t;
       // coupling c_j of this column (and of the separator that follows)
-      C* cslot = slot + (long long)(W + d.d_out) * LD;
+      C* cslot = slot + (long long)(W + d.d_out) * LDP;
       if (lane < W) cslot[lane] = coupling<R>(a, d, s2, j, lane);
       __syncwarp();
     }
     if (has_right) {
       const int s = r + 1;
-      C* cslot = fac + (long long)s * pe + (long long)(W + d.d_out) * LD;
+      C* cslot = fac + (long long)s * pe + (long long)(W + d.d_out) * LDP;
       if (lane < W) cslot[lane] = coupling<R>(a, d, s2, s, lane);
     }
     if (!ok && lane == 0) set_status(a.status, HS_EBREAKDOWN, bi, l);
@@ -280,7 +283,8 @@ __global__ void __launch_bounds__(32) factor_chunks_kernel(FactorArgs a) {
 template <typename R, int W>
 __global__ void __launch_bounds__(32) factor_reduced_kernel(FactorArgs a) {
   using C = cplx<R>;
-  constexpr int LD = W + 1;
+  constexpr int LD = W + 1;          // shared work matrices and corner blocks
+  constexpr int LDP = W + 2;         // global payload rows (payload_ld)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* bufA = reinterpret_cast<C*>(smem_raw);
   C* bufG = bufA + W * LD;
@@ -356,10 +360,10 @@ __global__ void __launch_bounds__(32) factor_reduced_kernel(FactorArgs a) {
           }
         }
         __syncwarp();
-        store_rows<R, W>(red + (long long)W * LD, F, lane, 0, W);
+        store_rows<R, W>(red + (long long)W * LDP, F, lane, 0, W, LDP);
       }
       ok &= invert_inplace<R, W>(A, piv, lane);
-      store_rows<R, W>(red, A, lane, 0, W);
+      store_rows<R, W>(red, A, lane, 0, W, LDP);
       C* t = A; A = Gam; Gam = t;
       __syncwarp();
     }

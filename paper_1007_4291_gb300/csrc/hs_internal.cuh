@@ -6,7 +6,7 @@
 #include <vector>
 #include <string>
 #include <atomic>
-#include "../../include/hs.h"
+#include "hs.h"
 
 namespace hs {
 

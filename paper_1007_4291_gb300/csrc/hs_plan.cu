@@ -113,7 +113,7 @@ extern "C" int hs_default_options(hs_options* opt) {
   opt->chunk = 0;
   opt->max_nrhs = 64;
   opt->restart = 20;
-  opt->reorth = 1;
+  opt->reorth = 0;
   opt->spin_budget = 1LL << 30;
   return HS_OK;
 }
@@ -203,7 +203,10 @@ extern "C" int hs_setup(const double* c, double omega, int n, int dim, int pml_w
     Wmax = std::max(Wmax, d.W);
   }
   // x1 chunking of the subproblem solves (>= 2 columns per chunk).
+  // (at most 64 separators: the separator solve keeps their right-hand
+  // sides in shared memory)
   p->L = opt.chunk ? opt.chunk : 32;
+  p->L = std::max(p->L, (n + 64) / 65);
   if (p->L > n) p->L = n;
   if (p->L < 2) p->L = 2;
   p->P = (n + p->L - 1) / p->L;

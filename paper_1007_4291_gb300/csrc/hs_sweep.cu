@@ -49,36 +49,6 @@ struct SweepArgs {
 
 template <int W> struct TPR { static constexpr int value = (W >= 24) ? 8 : 4; };
 
-template <typename R>
-__device__ __forceinline__ cplx<R> ncoup(const SweepArgs& a, int row, int j) {
-  // x2 coupling N_{i,row} of A between grid rows row and row+1 at column i = j+1
-  const cplx<R>* a2 = reinterpret_cast<const cplx<R>*>(a.a2);
-  const cplx<R>* is1 = reinterpret_cast<const cplx<R>*>(a.inv_s1);
-  return cmul(a2[row], is1[j + 1]);
-}
-
-// Right-hand side of T~_B at window row p, column j, RHS r.
-template <typename R>
-__device__ __forceinline__ cplx<R> sweep_input(const SweepArgs& a, const BlockDesc& d, int p, int j, int r) {
-  const cplx<R>* u = reinterpret_cast<const cplx<R>*>(a.u);
-  const long long rs = (long long)a.n * a.R;
-  if (a.mode == 0) {
-    if (p < d.out_off || p >= d.out_off + d.d_out) return cplx<R>{0, 0};
-    const int jg = d.wlo + p;
-    cplx<R> v = u[(jg - 1) * rs + (long long)j * a.R + r];
-    if (jg == d.lo && d.prev_lo_row)
-      cfms(v, ncoup<R>(a, d.lo - 1, j), u[(d.prev_lo_row - 1) * rs + (long long)j * a.R + r]);
-    if (jg == d.hi && d.prev_hi_row)
-      cfms(v, ncoup<R>(a, d.hi, j), u[(d.prev_hi_row - 1) * rs + (long long)j * a.R + r]);
-    return v;
-  } else {
-    if (p != d.coup_local) return cplx<R>{0, 0};
-    const int jg = d.wlo + p;
-    const int rowN = min(jg, d.next_row);
-    return cmul(ncoup<R>(a, rowN, j), u[(d.next_row - 1) * rs + (long long)j * a.R + r]);
-  }
-}
-
 // Gather the full W-vector from the T lanes of this RHS (each owns ROWS rows).
 template <typename R, int W, int T>
 __device__ __forceinline__ void allgather(const cplx<R> (&own)[W / T], cplx<R> (&full)[W]) {
@@ -90,410 +60,724 @@ __device__ __forceinline__ void allgather(const cplx<R> (&own)[W / T], cplx<R> (
   }
 }
 
-// After a wait has expired: give the copies still in flight (uses t and t+1
-// of the two barriers) one more bounded wait before the CTA exits.
-__device__ __forceinline__ void drain_inflight(uint64_t* bars, int t, int nuses, long long spin) {
-  if (threadIdx.x == 0) {
-    for (int u = t; u < t + 2 && u < nuses; ++u) (void)mbar_wait_bounded(&bars[u & 1], (u >> 1) & 1, spin);
-  }
-}
+constexpr int S13 = 4;        // TMA ring depth of the chunk kernels (phases 1 and 3)
+constexpr int NCW = NT / 32;  // consumer warps per CTA; one more warp produces the ring
 
-template <typename R, int W>
-struct ChunkSmem {
-  static constexpr size_t bytes(int d_out) {
-    return 128 + 2 * (((size_t)payload_elems(W, d_out) * sizeof(cplx<R>) + 127) / 128 * 128);
+__host__ __device__ __forceinline__ size_t round128(size_t b) { return (b + 127) / 128 * 128; }
+
+// Per-thread description of the right-hand side of T~_B on the thread's own
+// window rows: a direct term (forward sweep: the block rows of u) and up to
+// two coupling terms k * inv_s1(j) * u[row'] (forward sweep: minus the
+// coupling to the previous blocks' rows; backward sweep: the coupling to the
+// next block's row).  Offsets count rows of u (n*R elements); -1 = none.
+template <typename R, int ROWS>
+struct RhsTerms {
+  int drow[ROWS], crow1[ROWS], crow2[ROWS];
+  cplx<R> k1[ROWS], k2[ROWS];
+
+  // own rows p0, p0 + pstride, ..., p0 + (ROWS-1) pstride
+  __device__ __forceinline__ void init(const SweepArgs& a, const BlockDesc& d, int p0, int pstride = 1) {
+    const cplx<R>* a2 = reinterpret_cast<const cplx<R>*>(a.a2);
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+      const int p = p0 + q * pstride, jg = d.wlo + p;
+      drow[q] = crow1[q] = crow2[q] = -1;
+      k1[q] = k2[q] = cplx<R>{0, 0};
+      if (a.mode == 0) {
+        if (p >= d.out_off && p < d.out_off + d.d_out) {
+          drow[q] = jg - 1;
+          if (jg == d.lo && d.prev_lo_row) { crow1[q] = d.prev_lo_row - 1; k1[q] = cplx<R>{-a2[d.lo - 1].re, -a2[d.lo - 1].im}; }
+          if (jg == d.hi && d.prev_hi_row) { crow2[q] = d.prev_hi_row - 1; k2[q] = cplx<R>{-a2[d.hi].re, -a2[d.hi].im}; }
+        }
+      } else if (p == d.coup_local) {
+        crow1[q] = d.next_row - 1;
+        k1[q] = a2[min(jg, d.next_row)];
+      }
+    }
+  }
+  // Raw operands of the right-hand side at column j (loads only; combine()
+  // forms the value later, so the loads can be in flight meanwhile).
+  struct Raw {
+    cplx<R> d[ROWS], c1[ROWS], c2[ROWS], s;
+  };
+  __device__ __forceinline__ void load_raw(Raw& w, const cplx<R>* ur, const cplx<R>* is1, int n, int R_,
+                                           int j) const {
+    w.s = is1[j + 1];
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+      w.d[q] = (drow[q] >= 0) ? ur[((long long)drow[q] * n + j) * R_] : cplx<R>{0, 0};
+      w.c1[q] = (crow1[q] >= 0) ? ur[((long long)crow1[q] * n + j) * R_] : cplx<R>{0, 0};
+      w.c2[q] = (crow2[q] >= 0) ? ur[((long long)crow2[q] * n + j) * R_] : cplx<R>{0, 0};
+    }
+  }
+  __device__ __forceinline__ void combine(cplx<R> (&g)[ROWS], const Raw& w) const {
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+      cplx<R> v = w.d[q];
+      if (crow1[q] >= 0) cfma(v, cmul(k1[q], w.s), w.c1[q]);
+      if (crow2[q] >= 0) cfma(v, cmul(k2[q], w.s), w.c2[q]);
+      g[q] = v;
+    }
+  }
+  // right-hand side at column j for the RHS whose first element is ur = u + r
+  __device__ __forceinline__ void load(cplx<R> (&g)[ROWS], const cplx<R>* ur, const cplx<R>* is1, int n, int R_,
+                                       int j) const {
+    const cplx<R> s = is1[j + 1];
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+      cplx<R> v{0, 0};
+      if (drow[q] >= 0) v = ur[((long long)drow[q] * n + j) * R_];
+      if (crow1[q] >= 0) cfma(v, cmul(k1[q], s), ur[((long long)crow1[q] * n + j) * R_]);
+      if (crow2[q] >= 0) cfma(v, cmul(k2[q], s), ur[((long long)crow2[q] * n + j) * R_]);
+      g[q] = v;
+    }
   }
 };
 
-// ---------------------------------------------------------------- phase 1
+// Shared-memory bytes of the chunk kernels: barriers, S13 ring stages each
+// holding the column payload and (phase 3) this CTA's tile of the z store,
+// and (phase 3) the left-separator vectors of the CTA's RHS.
 template <typename R, int W, int T>
-__global__ void __launch_bounds__(NT) phase1_kernel(SweepArgs a) {
+size_t chunk_smem(int d_out, bool p3) {
+  const size_t pb = round128((size_t)payload_elems(W, d_out) * sizeof(cplx<R>));
+  const size_t zb = p3 ? round128((size_t)(NT / T) * W * sizeof(cplx<R>)) : 0;
+  const size_t bb = p3 ? round128((size_t)(NT / T) * W * sizeof(cplx<R>)) : 0;
+  return 256 + S13 * (pb + zb) + bb;
+}
+
+// Producer warp of a ring: issues use t of nuses into stage t % S once the
+// consumers have released use t - S.  Returns after every copy it issued has
+// landed (bounded waits; an expired wait records HS_ETIMEOUT).
+template <typename F>
+__device__ __forceinline__ void ring_producer(uint64_t* full, uint64_t* empty, int S, int nuses, long long spin,
+                                              int* status, int front, F&& issue) {
+  int t = 0;
+  for (; t < nuses; ++t) {
+    if (t >= S && !mbar_wait_bounded(&empty[t % S], ((t / S) - 1) & 1, spin)) {
+      set_status(status, HS_ETIMEOUT, front, -4);
+      break;
+    }
+    issue(t);
+  }
+  for (int u = (t > S ? t - S : 0); u < t; ++u) (void)mbar_wait_bounded(&full[u % S], (u / S) & 1, spin);
+}
+
+// ---------------------------------------------------------------- phases 1 and 3
+// One CTA owns one chunk of one block for a group of RG right-hand sides.
+// Each consumer thread owns a tile of ROWS window rows x RPT RHS; the
+// per-column product (W x W) * (W x RG) reads G_j from the TMA ring and the
+// vector being carried from shared memory (written by its owners before a
+// named barrier), so every column costs one barrier.  A producer warp streams
+// the column payloads.
+template <typename R, int W> struct Tile13 {
+  static constexpr int ROWS = (W == 12) ? 3 : W / 8;  // window rows per thread
+  static constexpr int NRG = W / ROWS;                // row groups
+  static constexpr int RPT = 2;                       // RHS per thread
+  static constexpr int RG = sizeof(R) == 4 ? 64 : 32; // RHS per CTA
+  static constexpr int NHG = RG / RPT;                // RHS groups
+  static constexpr int NCONS = NRG * NHG;             // consumer threads
+  static constexpr int LDR = RG + 2;                  // row stride of the [W][RG] exchange arrays
+};
+
+// Two adjacent complex values of shared memory (one 128-bit access for c64).
+template <typename R>
+__device__ __forceinline__ void ld2(const cplx<R>* p, cplx<R>& a, cplx<R>& b) {
+  a = p[0];
+  b = p[1];
+}
+template <>
+__device__ __forceinline__ void ld2<float>(const cplx<float>* p, cplx<float>& a, cplx<float>& b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = cplx<float>{v.x, v.y};
+  b = cplx<float>{v.z, v.w};
+}
+template <typename R>
+__device__ __forceinline__ void st2(cplx<R>* p, cplx<R> a, cplx<R> b) {
+  p[0] = a;
+  p[1] = b;
+}
+template <>
+__device__ __forceinline__ void st2<float>(cplx<float>* p, cplx<float> a, cplx<float> b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.re, a.im, b.re, b.im);
+}
+
+__device__ __forceinline__ void consumer_barrier(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Shared-memory bytes of phases 1 and 3.
+template <typename R, int W>
+size_t tile_smem(int d_out, bool p3) {
+  using TL = Tile13<R, W>;
+  const size_t pb = round128((size_t)payload_elems(W, d_out) * sizeof(cplx<R>));
+  const size_t vb = round128((size_t)W * TL::LDR * sizeof(cplx<R>));  // one W x RG array (padded)
+  // phase 1: ring of payloads, Y and g double buffers
+  // phase 3: ring of (payload + z tile), tv double buffer, beta
+  return p3 ? 256 + S13 * (pb + vb) + 3 * vb : 256 + S13 * pb + 4 * vb;
+}
+
+// Forward elimination over the chunk's interior columns:
+//   y_j = g_j - C_{j-1} z_{j-1},  z_j = G_j y_j  (z_j stored for phase 3),
+// the left-spike sum sum_j W_j^t g_j, and the separator term C_r z_r - g(s).
+// Thread (rg, hg) owns rows rg + NRG*i (i < ROWS) and RHS 2hg, 2hg+1 of the group.
+template <typename R, int W>
+__global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase1_kernel(SweepArgs a) {
   using C = cplx<R>;
-  constexpr int ROWS = W / T, LD = W + 1;
-  constexpr int RT = NT / T;
+  using TL = Tile13<R, W>;
+  constexpr int ROWS = TL::ROWS, NRG = TL::NRG, RPT = TL::RPT, RG = TL::RG, NCONS = TL::NCONS, LDR = TL::LDR;
+  constexpr int LDP = W + 2;
+  static_assert(RPT == 2, "tiles carry two right-hand sides");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* empty = full + S13;
   const int front = blockIdx.z, k = blockIdx.x;
   const BlockDesc& d = a.blk[front];
   const long long pe = payload_elems(W, d.d_out);
   const uint32_t pbytes = (uint32_t)(pe * sizeof(C));
-  const size_t bstride = ((size_t)pbytes + 127) / 128 * 128;
-  C* buf0 = reinterpret_cast<C*>(smem_raw + 128);
-  C* buf1 = reinterpret_cast<C*>(smem_raw + 128 + bstride);
+  const size_t pstride = round128(pbytes);
+  const size_t vb = round128((size_t)W * LDR * sizeof(C));
+  C* ybuf = reinterpret_cast<C*>(smem_raw + 256 + S13 * pstride);            // [2][W][LDR]
+  C* gbuf = reinterpret_cast<C*>(smem_raw + 256 + S13 * pstride + 2 * vb);   // [2][W][LDR]
   const C* fac = reinterpret_cast<const C*>(a.fac) + d.fac_off;
-  const int tid = threadIdx.x, sl = tid % T;
-  const int r = blockIdx.y * RT + tid / T;
-  const bool valid = r < a.R;
-  const int rr = (r < a.R) ? r : (a.R - 1);
+  const int tid = threadIdx.x;
   const int l = k * a.L;
   const int rgt = (k < a.P - 1) ? (k + 1) * a.L - 2 : a.n - 1;
   const int ncol = rgt - l + 1;
-  const bool has_left = k > 0;
+  auto stage = [&](int u) { return reinterpret_cast<const C*>(smem_raw + 256 + (size_t)(u % S13) * pstride); };
 
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int u = 0; u < S13; ++u) {
+      mbar_init(&full[u], 1);
+      mbar_init(&empty[u], 1);
+    }
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&bars[0], pbytes);
-    tma_bulk_g2s(buf0, fac + (long long)l * pe, pbytes, &bars[0]);
-    if (ncol > 1) {
-      mbar_arrive_expect_tx(&bars[1], pbytes);
-      tma_bulk_g2s(buf1, fac + (long long)(l + 1) * pe, pbytes, &bars[1]);
-    }
+  if (tid >= NCONS) {
+    if (tid == NCONS)
+      ring_producer(full, empty, S13, ncol, a.spin, a.status, front, [&](int t) {
+        mbar_arrive_expect_tx(&full[t % S13], pbytes);
+        tma_bulk_g2s(const_cast<C*>(stage(t)), fac + (long long)(l + t) * pe, pbytes, &full[t % S13]);
+      });
+    return;
   }
-  C y[W], acc[W], zown[ROWS], cprev[ROWS];
+  const int rg = tid % NRG, hg = tid / NRG;
+  const int c0 = hg * RPT;                 // first own RHS of the group
+  const int rbase = blockIdx.y * RG;
+  bool valid[RPT];
+  const C* ur[RPT];
 #pragma unroll
-  for (int q = 0; q < W; ++q) acc[q] = C{0, 0};
-#pragma unroll
-  for (int q = 0; q < ROWS; ++q) { zown[q] = C{0, 0}; cprev[q] = C{0, 0}; }
-  C* zst = reinterpret_cast<C*>(a.z) + ((long long)front * a.n * a.R) * W;
+  for (int q = 0; q < RPT; ++q) {
+    valid[q] = rbase + c0 + q < a.R;
+    ur[q] = reinterpret_cast<const C*>(a.u) + min(rbase + c0 + q, a.R - 1);
+  }
+  const C* is1 = reinterpret_cast<const C*>(a.inv_s1);
+  RhsTerms<R, ROWS> rhs;
+  rhs.init(a, d, rg, NRG);
+  const bool has_left = k > 0;
+  const int in_lo = (a.mode == 0) ? d.out_off : d.coup_local;
+  const int in_hi = (a.mode == 0) ? d.out_off + d.d_out : d.coup_local + 1;
+  C* zbase = reinterpret_cast<C*>(a.z) + ((long long)front * a.n * a.R) * W;
 
-  for (int t = 0; t < ncol; ++t) {
+  using Raw = typename RhsTerms<R, ROWS>::Raw;
+  auto load_g = [&](C (&g)[RPT][ROWS], int j) {
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) rhs.load(g[q], ur[q], is1, a.n, a.R, j);
+  };
+  auto load_raw = [&](Raw (&w)[RPT], int j) {
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) rhs.load_raw(w[q], ur[q], is1, a.n, a.R, j);
+  };
+  auto put_tile = [&](C* buf, const C (&v)[RPT][ROWS]) {
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i) st2(buf + (rg + NRG * i) * LDR + c0, v[0][i], v[1][i]);
+  };
+  C z[RPT][ROWS], sp[RPT][ROWS];
+  Raw ra[RPT], rb[RPT];   // raw right-hand sides, fetched two columns ahead
+#pragma unroll
+  for (int q = 0; q < RPT; ++q)
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i) sp[q][i] = C{0, 0};
+  {
+    C g0[RPT][ROWS];
+    load_g(g0, l);
+    put_tile(ybuf, g0);     // y_l = g_l
+    put_tile(gbuf, g0);
+  }
+  if (ncol > 1) load_raw(ra, l + 1);
+  if (ncol > 2) load_raw(rb, l + 2);
+  consumer_barrier(NCONS);
+  bool ok = true;
+  // one column step; wn = raw right-hand side of the next column
+  auto step = [&](int t, const Raw (&wn)[RPT]) {
     const int j = l + t;
-    const int b = t & 1;
-    const C* G = b ? buf1 : buf0;
-    const C* V = G + W * LD;
-    const C* cc = V + d.d_out * LD;
-    const bool ok = mbar_wait_bounded(&bars[b], (t >> 1) & 1, a.spin);
-    C g[ROWS], yown[ROWS];
+    const C* G = stage(t);
+    const C* V = G + W * LDP;
+    const C* cc = V + d.d_out * LDP;
+    const C* Y = ybuf + (t & 1) * (W * LDR);
+    const C* Gi = gbuf + (t & 1) * (W * LDR);
+    ok = mbar_wait_bounded(&full[t % S13], (t / S13) & 1, a.spin);
+    if (!ok) return;
 #pragma unroll
-    for (int q = 0; q < ROWS; ++q) {
-      const int p = sl * ROWS + q;
-      g[q] = sweep_input<R>(a, d, p, j, rr);
-      yown[q] = g[q];
-      if (t > 0) cfms(yown[q], cprev[q], zown[q]);
-    }
-    allgather<R, W, T>(yown, y);
+    for (int q = 0; q < RPT; ++q)
 #pragma unroll
-    for (int q = 0; q < ROWS; ++q) {
-      const int p = sl * ROWS + q;
-      C s0{0, 0}, s1{0, 0};
+      for (int i = 0; i < ROWS; ++i) z[q][i] = C{0, 0};
 #pragma unroll
-      for (int qq = 0; qq < W; qq += 2) {
-        cfma(s0, G[p * LD + qq], y[qq]);
-        cfma(s1, G[p * LD + qq + 1], y[qq + 1]);
+    for (int kk = 0; kk < W; kk += 2) {
+      C g0[ROWS], g1[ROWS], y00, y01, y10, y11;
+#pragma unroll
+      for (int i = 0; i < ROWS; ++i) ld2(G + (rg + NRG * i) * LDP + kk, g0[i], g1[i]);
+      ld2(Y + kk * LDR + c0, y00, y01);
+      ld2(Y + (kk + 1) * LDR + c0, y10, y11);
+#pragma unroll
+      for (int i = 0; i < ROWS; ++i) {
+        cfma(z[0][i], g0[i], y00);
+        cfma(z[1][i], g0[i], y01);
+        cfma(z[0][i], g1[i], y10);
+        cfma(z[1][i], g1[i], y11);
       }
-      zown[q] = cadd(s0, s1);
-      cprev[q] = cc[p];
     }
-    if (valid) {
-      C* zp = zst + ((long long)j * a.R + r) * W + sl * ROWS;
+    // store z_j (layout [front][col][rhs][W])
 #pragma unroll
-      for (int q = 0; q < ROWS; ++q) zp[q] = zown[q];
-    }
+    for (int q = 0; q < RPT; ++q)
+      if (valid[q]) {
+        C* zp = zbase + ((long long)j * a.R + rbase + c0 + q) * W + rg;
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) zp[NRG * i] = z[q][i];
+      }
     if (has_left) {
+      // sp[own rows] += sum over input rows o of W_j[o][own rows] g_j[o]
+      for (int o = in_lo; o < in_hi; ++o) {
+        const C* vr = V + (o - d.out_off) * LDP + rg;
+        C go0, go1;
+        ld2(Gi + o * LDR + c0, go0, go1);
 #pragma unroll
-      for (int q = 0; q < ROWS; ++q) {
-        const int p = sl * ROWS + q;
-        if (p >= d.out_off && p < d.out_off + d.d_out) {
-          const C* vr = V + (p - d.out_off) * LD;
-#pragma unroll
-          for (int qq = 0; qq < W; ++qq) cfma(acc[qq], vr[qq], g[q]);
+        for (int i = 0; i < ROWS; ++i) {
+          const C v = vr[NRG * i];
+          cfma(sp[0][i], v, go0);
+          cfma(sp[1][i], v, go1);
         }
       }
     }
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) set_status(a.status, HS_ETIMEOUT, front, j);
-      drain_inflight(bars, t, ncol, a.spin);
-      return;
+    if (t + 1 < ncol) {
+      // y_{j+1} = g_{j+1} - C_j z_j
+      C gn[RPT][ROWS], yn[RPT][ROWS];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) rhs.combine(gn[q], wn[q]);
+#pragma unroll
+      for (int i = 0; i < ROWS; ++i) {
+        const C ci = cc[rg + NRG * i];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          yn[q][i] = gn[q][i];
+          cfms(yn[q][i], ci, z[q][i]);
+        }
+      }
+      put_tile(ybuf + ((t + 1) & 1) * (W * LDR), yn);
+      put_tile(gbuf + ((t + 1) & 1) * (W * LDR), gn);
     }
-    if (tid == 0 && t + 2 < ncol) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&bars[b], pbytes);
-      tma_bulk_g2s(b ? buf1 : buf0, fac + (long long)(j + 2) * pe, pbytes, &bars[b]);
+    consumer_barrier(NCONS);
+    if (tid == 0) mbar_arrive(&empty[t % S13]);
+  };
+  for (int t = 0; t < ncol; t += 2) {
+    step(t, ra);
+    if (!ok) break;
+    if (t + 3 < ncol) load_raw(ra, l + t + 3);
+    if (t + 1 < ncol) {
+      step(t + 1, rb);
+      if (!ok) break;
+      if (t + 4 < ncol) load_raw(rb, l + t + 4);
     }
   }
-  // separator contributions
-  const long long sep_base = ((long long)front * a.P + k) * a.R;
-  if (k < a.P - 1 && valid) {
-    C* rc = reinterpret_cast<C*>(a.rc) + (sep_base + r) * W + sl * ROWS;
+  if (!ok) {
+    if ((tid & 31) == 0) set_status(a.status, HS_ETIMEOUT, front, l);
+    return;
+  }
+  // separator contributions (z holds z_r of the last column)
+  const long long sep_base = ((long long)front * a.P + k) * a.R + rbase + c0;
+  const C* cr = fac + (long long)rgt * pe + (long long)(W + d.d_out) * LDP;   // c_r
+  if (k < a.P - 1) {
+    C gs[RPT][ROWS];
+    load_g(gs, rgt + 1);
 #pragma unroll
-    for (int q = 0; q < ROWS; ++q) rc[q] = cmul(cprev[q], zown[q]);
+    for (int q = 0; q < RPT; ++q)
+      if (valid[q]) {
+        C* rc = reinterpret_cast<C*>(a.rc) + (sep_base + q) * W + rg;
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) rc[NRG * i] = csub(cmul(cr[rg + NRG * i], z[q][i]), gs[q][i]);
+      }
   }
   if (has_left) {
+    const C* cl = fac + (long long)(l - 1) * pe + (long long)(W + d.d_out) * LDP;   // c_{l-1}
 #pragma unroll
-    for (int m = 1; m < T; m <<= 1) {
+    for (int q = 0; q < RPT; ++q)
+      if (valid[q]) {
+        C* lc = reinterpret_cast<C*>(a.lc) + (sep_base + q) * W + rg;
 #pragma unroll
-      for (int qq = 0; qq < W; ++qq) acc[qq] = cadd(acc[qq], shfl_xor_c(acc[qq], m, T));
-    }
-    if (valid) {
-      const C* cl = fac + (long long)(l - 1) * pe + (long long)(W + d.d_out) * LD;  // c_{l-1}
-      C* lc = reinterpret_cast<C*>(a.lc) + (sep_base + r) * W + sl * ROWS;
-#pragma unroll
-      for (int q = 0; q < ROWS; ++q) {
-        C av{0, 0};
-#pragma unroll
-        for (int s = 0; s < T; ++s)
-          if (s == sl) av = acc[s * ROWS + q];  // static register index
-        lc[q] = cmul(cl[sl * ROWS + q], av);
+        for (int i = 0; i < ROWS; ++i) lc[NRG * i] = cmul(cl[rg + NRG * i], sp[q][i]);
       }
-    }
   }
 }
 
 // ---------------------------------------------------------------- phase 2
-// One warp per right-hand side, lane p = window row p (p < W).
+// Block LU solve of the separator system, one warp per RHS (lane p = row p),
+// warps independent.  rho_k = -(rc_k + lc_{k+1}) of every separator is
+// gathered into shared memory first (two independent loads per value); the
+// forward chain psi_k = rho_k - F_k psi_{k-1} keeps psi_k there, and the
+// backward chain x_k = Gamma_k psi_k - F_{k+1}^t x_{k+1} reads it back.  The
+// chain variable is exchanged through shared memory (broadcast loads).  A
+// producer warp streams (Gamma_k | F_k) through an S2-deep TMA ring (forward
+// order, then backward order).
+constexpr int WPC = NT / 32;  // RHS (consumer warps) per CTA in phase 2
+constexpr int S2 = 4;         // TMA ring depth of phase 2
+
 template <typename R, int W>
-__global__ void __launch_bounds__(NT) phase2_kernel(SweepArgs a) {
+size_t phase2_smem(int nsep) {
+  return 256 + (size_t)S2 * round128((size_t)red_elems(W) * sizeof(cplx<R>)) +
+         (size_t)WPC * (nsep + 1) * W * sizeof(cplx<R>);
+}
+
+template <typename R, int W>
+__global__ void __launch_bounds__(NT + 32) phase2_kernel(SweepArgs a) {
   using C = cplx<R>;
-  constexpr int LD = W + 1;
-  constexpr int WPC = NT / 32;
+  constexpr int LDP = W + 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* empty = full + S2;
   const int front = blockIdx.z;
   const BlockDesc& d = a.blk[front];
   const long long re = red_elems(W);
   const uint32_t rbytes = (uint32_t)(re * sizeof(C));
-  const size_t bstride = ((size_t)rbytes + 127) / 128 * 128;
-  C* buf0 = reinterpret_cast<C*>(smem_raw + 128);
-  C* buf1 = reinterpret_cast<C*>(smem_raw + 128 + bstride);
+  const size_t sstride = round128(rbytes);
+  const int nsep = a.P - 1;
+  const int nuses = 2 * nsep;
+  C* rz = reinterpret_cast<C*>(smem_raw + 256 + (size_t)S2 * sstride);
   const C* red = reinterpret_cast<const C*>(a.red) + d.red_off;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int r = blockIdx.y * WPC + tid / 32;
+  const int tid = threadIdx.x;
+  auto stage = [&](int u) { return reinterpret_cast<C*>(smem_raw + 256 + (size_t)(u % S2) * sstride); };
+  auto sep_of_use = [&](int u) { return (u < nsep) ? u : (nuses - 1 - u); };
+
+  if (tid == 0) {
+    for (int u = 0; u < S2; ++u) {
+      mbar_init(&full[u], 1);
+      mbar_init(&empty[u], WPC);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid >= NT) {
+    if (tid == NT)
+      ring_producer(full, empty, S2, nuses, a.spin, a.status, front, [&](int t) {
+        mbar_arrive_expect_tx(&full[t % S2], rbytes);
+        tma_bulk_g2s(stage(t), red + (long long)sep_of_use(t) * re, rbytes, &full[t % S2]);
+      });
+    return;
+  }
+  const int lane = tid & 31, wq = tid >> 5;
+  const int r = blockIdx.y * WPC + wq;
   const bool valid = r < a.R;
   const int rr = valid ? r : (a.R - 1);
-  const int nsep = a.P - 1;
   const int pl = lane < W ? lane : 0;
   const C* rcb = reinterpret_cast<const C*>(a.rc);
   const C* lcb = reinterpret_cast<const C*>(a.lc);
   C* xsb = reinterpret_cast<C*>(a.xs);
-  C* psb = reinterpret_cast<C*>(a.ps);
   const long long fb = (long long)front * a.P;
-
-  if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (tid == 0) {
-    // payload use t reads separator t (forward, t < nsep) or 2 nsep - 1 - t
-    // (backward); 2 nsep >= 2 uses always exist.
-    const int k1 = (1 < nsep) ? 1 : 2 * nsep - 2;
-    mbar_arrive_expect_tx(&bars[0], rbytes);
-    tma_bulk_g2s(buf0, red, rbytes, &bars[0]);
-    mbar_arrive_expect_tx(&bars[1], rbytes);
-    tma_bulk_g2s(buf1, red + (long long)k1 * re, rbytes, &bars[1]);
-  }
-  // Forward: psi_k = rho_k - F_k psi_{k-1};  zeta_k = Gamma_k psi_k (stored)
-  C psi{0, 0};
-  int t = 0;  // barrier use counter
-  for (int k = 0; k < nsep; ++k, ++t) {
-    const int b = t & 1;
-    const C* Gm = b ? buf1 : buf0;
-    const C* F = Gm + W * LD;
-    const bool ok = mbar_wait_bounded(&bars[b], (t >> 1) & 1, a.spin);
-    const int s = (k + 1) * a.L - 1;
-    C rho = sweep_input<R>(a, d, pl, s, rr);
-    rho = csub(rho, rcb[((fb + k) * a.R + rr) * W + pl]);
-    rho = csub(rho, lcb[((fb + k + 1) * a.R + rr) * W + pl]);
-    C np = rho;
-    if (k > 0) {
+  C* myrz = rz + (size_t)wq * (nsep + 1) * W;   // nsep psi vectors + one exchange slot
+  C* xch = myrz + (size_t)nsep * W;
+  // rho_k for every separator (all loads issued before any use)
+  for (int k0 = 0; k0 < nsep; k0 += 16) {
+    C v1[16], v2[16];
 #pragma unroll
-      for (int q = 0; q < W; ++q) cfms(np, F[pl * LD + q], shfl_c(psi, q));
+    for (int q = 0; q < 16; ++q) {
+      const int k = min(k0 + q, nsep - 1);
+      v1[q] = rcb[((fb + k) * a.R + rr) * W + pl];
+      v2[q] = lcb[((fb + k + 1) * a.R + rr) * W + pl];
     }
-    psi = np;
-    C zeta{0, 0};
 #pragma unroll
-    for (int q = 0; q < W; ++q) cfma(zeta, Gm[pl * LD + q], shfl_c(psi, q));
-    if (valid && lane < W) psb[((fb + k) * a.R + r) * W + lane] = zeta;
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) set_status(a.status, HS_ETIMEOUT, front, -2);
-      drain_inflight(bars, t, 2 * nsep, a.spin);
-      return;
-    }
-    if (tid == 0) {
-      // next payload: forward continues with k+2, then the backward pass
-      // reads separators nsep-1 down to 0.
-      const int nt = t + 2;
-      int kk = -1;
-      if (nt < nsep) kk = nt;
-      else if (nt < 2 * nsep) kk = 2 * nsep - 1 - nt;
-      if (kk >= 0) {
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bars[b], rbytes);
-        tma_bulk_g2s(b ? buf1 : buf0, red + (long long)kk * re, rbytes, &bars[b]);
-      }
-    }
+    for (int q = 0; q < 16; ++q)
+      if (k0 + q < nsep && lane < W) myrz[(k0 + q) * W + lane] = C{-(v1[q].re + v2[q].re), -(v1[q].im + v2[q].im)};
   }
   __syncwarp();
-  // Backward: x_k = zeta_k - F_{k+1}^t x_{k+1}; the payload of separator k
-  // holds F_k, so the product with F_{k+1} uses the previous payload, kept
-  // in registers as this lane's column of F_{k+1}.
-  C x{0, 0};
-  C fcol[W];
-  for (int k = nsep - 1; k >= 0; --k, ++t) {
-    const int b = t & 1;
-    const C* Gm = b ? buf1 : buf0;
-    const C* F = Gm + W * LD;
-    const bool ok = mbar_wait_bounded(&bars[b], (t >> 1) & 1, a.spin);
-    C xn = psb[((fb + k) * a.R + rr) * W + pl];
-    if (k < nsep - 1) {
+  bool ok = true;
+  int t = 0;
+  for (int k = 0; k < nsep; ++k, ++t) {
+    const C* F = stage(t) + W * LDP;
+    ok = mbar_wait_bounded(&full[t % S2], (t / S2) & 1, a.spin);
+    if (!ok) break;
+    C s0 = myrz[k * W + pl], s1{0, 0}, s2{0, 0}, s3{0, 0};
+    if (k > 0) {
+      const C* fr = F + pl * LDP;
+      const C* pv = myrz + (k - 1) * W;     // psi_{k-1}, read by every lane
 #pragma unroll
-      for (int q = 0; q < W; ++q) cfms(xn, fcol[q], shfl_c(x, q));
-    }
-    x = xn;
-#pragma unroll
-    for (int q = 0; q < W; ++q) fcol[q] = F[q * LD + pl];
-    if (valid && lane < W) xsb[((fb + k) * a.R + r) * W + lane] = x;
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) set_status(a.status, HS_ETIMEOUT, front, -3);
-      drain_inflight(bars, t, 2 * nsep, a.spin);
-      return;
-    }
-    if (tid == 0) {
-      const int nt = t + 2;
-      if (nt < 2 * nsep) {
-        const int kk = 2 * nsep - 1 - nt;
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bars[b], rbytes);
-        tma_bulk_g2s(b ? buf1 : buf0, red + (long long)kk * re, rbytes, &bars[b]);
+      for (int q = 0; q < W; q += 4) {
+        cfms(s0, fr[q], pv[q]);
+        cfms(s1, fr[q + 1], pv[q + 1]);
+        cfms(s2, fr[q + 2], pv[q + 2]);
+        cfms(s3, fr[q + 3], pv[q + 3]);
       }
     }
+    const C psi = cadd(cadd(s0, s1), cadd(s2, s3));
+    __syncwarp();
+    if (lane < W) myrz[k * W + lane] = psi;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[t % S2]);
   }
+  C fcol[W];
+  for (int k = nsep - 1; k >= 0 && ok; --k, ++t) {
+    const C* Gm = stage(t);
+    const C* F = Gm + W * LDP;
+    ok = mbar_wait_bounded(&full[t % S2], (t / S2) & 1, a.spin);
+    if (!ok) break;
+    // Gamma_k psi_k: Gamma_k is symmetric, so lane p reads column p (no
+    // bank conflicts); psi_k is read by every lane
+    const C* ps = myrz + k * W;
+    C s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
+#pragma unroll
+    for (int q = 0; q < W; q += 4) {
+      cfma(s0, Gm[q * LDP + pl], ps[q]);
+      cfma(s1, Gm[(q + 1) * LDP + pl], ps[q + 1]);
+      cfma(s2, Gm[(q + 2) * LDP + pl], ps[q + 2]);
+      cfma(s3, Gm[(q + 3) * LDP + pl], ps[q + 3]);
+    }
+    if (k < nsep - 1) {
+#pragma unroll
+      for (int q = 0; q < W; q += 4) {   // x_{k+1} from the exchange slot
+        cfms(s0, fcol[q], xch[q]);
+        cfms(s1, fcol[q + 1], xch[q + 1]);
+        cfms(s2, fcol[q + 2], xch[q + 2]);
+        cfms(s3, fcol[q + 3], xch[q + 3]);
+      }
+    }
+    const C x = cadd(cadd(s0, s1), cadd(s2, s3));
+#pragma unroll
+    for (int q = 0; q < W; ++q) fcol[q] = F[q * LDP + pl];
+    __syncwarp();
+    if (lane < W) xch[lane] = x;
+    if (valid && lane < W) xsb[((fb + k) * a.R + r) * W + lane] = x;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[t % S2]);
+  }
+  if (!ok && lane == 0) set_status(a.status, HS_ETIMEOUT, front, -2);
 }
 
 // ---------------------------------------------------------------- phase 3
-template <typename R, int W, int T>
-__global__ void __launch_bounds__(NT) phase3_kernel(SweepArgs a) {
+// Back substitution over the chunk's interior columns from the right
+// separator: x_j = z_j - G_j (C_j x_{j+1}); output rows get the left-spike
+// correction -W_j beta, beta = C_{l-1} x_{left separator}.  Each ring stage
+// brings the column payload and the CTA's tile of the stored z_j.  Thread
+// (rg, hg) owns rows rg + NRG*i and RHS 2hg, 2hg+1 of the group.
+template <typename R, int W>
+__global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase3_kernel(SweepArgs a) {
   using C = cplx<R>;
-  constexpr int ROWS = W / T, LD = W + 1;
-  constexpr int RT = NT / T;
+  using TL = Tile13<R, W>;
+  constexpr int ROWS = TL::ROWS, NRG = TL::NRG, RPT = TL::RPT, RG = TL::RG, NCONS = TL::NCONS, LDR = TL::LDR;
+  constexpr int LDP = W + 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* empty = full + S13;
   const int front = blockIdx.z, k = blockIdx.x;
   const BlockDesc& d = a.blk[front];
   const long long pe = payload_elems(W, d.d_out);
   const uint32_t pbytes = (uint32_t)(pe * sizeof(C));
-  const size_t bstride = ((size_t)pbytes + 127) / 128 * 128;
-  C* buf0 = reinterpret_cast<C*>(smem_raw + 128);
-  C* buf1 = reinterpret_cast<C*>(smem_raw + 128 + bstride);
+  const size_t pstride = round128(pbytes);
+  const size_t vb = round128((size_t)W * LDR * sizeof(C));
+  const size_t sstride = pstride + vb;
+  C* tvbuf = reinterpret_cast<C*>(smem_raw + 256 + S13 * sstride);            // [2][W][LDR]
+  C* beta = reinterpret_cast<C*>(smem_raw + 256 + S13 * sstride + 2 * vb);     // [W][LDR]
   const C* fac = reinterpret_cast<const C*>(a.fac) + d.fac_off;
-  const int tid = threadIdx.x, sl = tid % T;
-  const int r = blockIdx.y * RT + tid / T;
-  const bool valid = r < a.R;
-  const int rr = valid ? r : (a.R - 1);
+  const int tid = threadIdx.x;
+  const int rbase = blockIdx.y * RG;
+  const int nvalid = min(RG, a.R - rbase);
+  const uint32_t zbytes = (uint32_t)((size_t)nvalid * W * sizeof(C));
   const int l = k * a.L;
   const int rgt = (k < a.P - 1) ? (k + 1) * a.L - 2 : a.n - 1;
   const int ncol = rgt - l + 1;
   const bool has_left = k > 0, has_right = k < a.P - 1;
-  C* u = reinterpret_cast<C*>(a.u);
-  const long long rs = (long long)a.n * a.R;
+  const C* zst = reinterpret_cast<const C*>(a.z) + ((long long)front * a.n * a.R) * W;
+  auto pay = [&](int t) { return reinterpret_cast<C*>(smem_raw + 256 + (size_t)(t % S13) * sstride); };
+  auto ztile = [&](int t) { return reinterpret_cast<C*>(smem_raw + 256 + (size_t)(t % S13) * sstride + pstride); };
 
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int u = 0; u < S13; ++u) {
+      mbar_init(&full[u], 1);
+      mbar_init(&empty[u], 1);
+    }
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&bars[0], pbytes);
-    tma_bulk_g2s(buf0, fac + (long long)rgt * pe, pbytes, &bars[0]);
-    if (ncol > 1) {
-      mbar_arrive_expect_tx(&bars[1], pbytes);
-      tma_bulk_g2s(buf1, fac + (long long)(rgt - 1) * pe, pbytes, &bars[1]);
-    }
+  if (tid >= NCONS) {
+    if (tid == NCONS)
+      ring_producer(full, empty, S13, ncol, a.spin, a.status, front, [&](int t) {
+        const int j = rgt - t;
+        mbar_arrive_expect_tx(&full[t % S13], pbytes + zbytes);
+        tma_bulk_g2s(pay(t), fac + (long long)j * pe, pbytes, &full[t % S13]);
+        tma_bulk_g2s(ztile(t), zst + ((long long)j * a.R + rbase) * W, zbytes, &full[t % S13]);
+      });
+    return;
+  }
+  const int rg = tid % NRG, hg = tid / NRG;
+  const int c0 = hg * RPT;
+  bool valid[RPT];
+  int rr[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    valid[q] = rbase + c0 + q < a.R;
+    rr[q] = min(rbase + c0 + q, a.R - 1);
   }
   const long long fb = (long long)front * a.P;
   const C* xsb = reinterpret_cast<const C*>(a.xs);
-  C xnext[W], beta[W];
+  C* u = reinterpret_cast<C*>(a.u);
+  const long long rs = (long long)a.n * a.R;
+  const bool bwd = a.mode == 1;
+  // beta = C_{l-1} x_{left separator}; x = x_{right separator} (own tile)
+  C x[RPT][ROWS];
+  {
+    const C* cl = fac + (long long)(l > 0 ? l - 1 : 0) * pe + (long long)(W + d.d_out) * LDP;
 #pragma unroll
-  for (int q = 0; q < W; ++q) {
-    xnext[q] = has_right ? xsb[((fb + k) * a.R + rr) * W + q] : C{0, 0};
-    beta[q] = C{0, 0};
-  }
-  if (has_left) {
-    const C* cl = fac + (long long)(l - 1) * pe + (long long)(W + d.d_out) * LD;
+    for (int i = 0; i < ROWS; ++i) {
+      const int p = rg + NRG * i;
+      C bv[RPT];
 #pragma unroll
-    for (int q = 0; q < W; ++q) beta[q] = cmul(cl[q], xsb[((fb + k - 1) * a.R + rr) * W + q]);
+      for (int q = 0; q < RPT; ++q) {
+        bv[q] = has_left ? cmul(cl[p], xsb[((fb + k - 1) * a.R + rr[q]) * W + p]) : C{0, 0};
+        x[q][i] = has_right ? xsb[((fb + k) * a.R + rr[q]) * W + p] : C{0, 0};
+      }
+      st2(beta + p * LDR + c0, bv[0], bv[1]);
+    }
   }
-  const C* zst = reinterpret_cast<const C*>(a.z) + ((long long)front * a.n * a.R) * W;
-  for (int t = 0; t < ncol; ++t) {
+  bool isout[ROWS];
+#pragma unroll
+  for (int i = 0; i < ROWS; ++i) isout[i] = (rg + NRG * i >= d.out_off) && (rg + NRG * i < d.out_off + d.d_out);
+  auto load_old = [&](C (&o)[RPT][ROWS], int j) {
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+#pragma unroll
+      for (int i = 0; i < ROWS; ++i)
+        o[q][i] = (bwd && isout[i]) ? u[(long long)(d.wlo + rg + NRG * i - 1) * rs + (long long)j * a.R + rr[q]]
+                                    : C{0, 0};
+  };
+  bool ok = true;
+  auto step = [&](int t, const C (&uo)[RPT][ROWS]) {
     const int j = rgt - t;
-    const int b = t & 1;
-    const C* G = b ? buf1 : buf0;
-    const C* V = G + W * LD;
-    const C* cc = V + d.d_out * LD;
-    const bool ok = mbar_wait_bounded(&bars[b], (t >> 1) & 1, a.spin);
-    C tv[W];
+    const C* G = pay(t);
+    const C* V = G + W * LDP;
+    const C* cc = V + d.d_out * LDP;
+    const C* zt = ztile(t);
+    C* TV = tvbuf + (t & 1) * (W * LDR);
+    ok = mbar_wait_bounded(&full[t % S13], (t / S13) & 1, a.spin);
+    if (!ok) return;
+    // tv = C_j x_{j+1} (own tile), shared through shared memory
 #pragma unroll
-    for (int q = 0; q < W; ++q) tv[q] = cmul(cc[q], xnext[q]);
-    C xown[ROWS];
-    const C* zp = zst + ((long long)j * a.R + rr) * W + sl * ROWS;
+    for (int i = 0; i < ROWS; ++i) {
+      const C ci = cc[rg + NRG * i];
+      st2(TV + (rg + NRG * i) * LDR + c0, cmul(ci, x[0][i]), cmul(ci, x[1][i]));
+    }
+    consumer_barrier(NCONS);
+    if (tid == 0 && t > 0) mbar_arrive(&empty[(t - 1) % S13]);   // every read of stage t-1 is done
 #pragma unroll
-    for (int q = 0; q < ROWS; ++q) {
-      const int p = sl * ROWS + q;
-      C s0 = zp[q], s1{0, 0};
+    for (int q = 0; q < RPT; ++q)
 #pragma unroll
-      for (int qq = 0; qq < W; qq += 2) {
-        cfms(s0, G[p * LD + qq], tv[qq]);
-        cfms(s1, G[p * LD + qq + 1], tv[qq + 1]);
+      for (int i = 0; i < ROWS; ++i) x[q][i] = zt[(c0 + q) * W + rg + NRG * i];
+#pragma unroll
+    for (int kk = 0; kk < W; kk += 2) {
+      C g0[ROWS], g1[ROWS], t00, t01, t10, t11;
+#pragma unroll
+      for (int i = 0; i < ROWS; ++i) ld2(G + (rg + NRG * i) * LDP + kk, g0[i], g1[i]);
+      ld2(TV + kk * LDR + c0, t00, t01);
+      ld2(TV + (kk + 1) * LDR + c0, t10, t11);
+#pragma unroll
+      for (int i = 0; i < ROWS; ++i) {
+        cfms(x[0][i], g0[i], t00);
+        cfms(x[1][i], g0[i], t01);
+        cfms(x[0][i], g1[i], t10);
+        cfms(x[1][i], g1[i], t11);
       }
-      xown[q] = cadd(s0, s1);
-      if (valid && p >= d.out_off && p < d.out_off + d.d_out) {
-        C o = xown[q];
+    }
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i) {
+      if (isout[i]) {
+        const int p = rg + NRG * i;
+        C o0 = x[0][i], o1 = x[1][i];
         if (has_left) {
-          const C* vr = V + (p - d.out_off) * LD;
-#pragma unroll
-          for (int qq = 0; qq < W; ++qq) cfms(o, vr[qq], beta[qq]);
+          const C* vr = V + (p - d.out_off) * LDP;
+#pragma unroll 4
+          for (int kk = 0; kk < W; kk += 2) {
+            C v0, v1, b00, b01, b10, b11;
+            ld2(vr + kk, v0, v1);
+            ld2(beta + kk * LDR + c0, b00, b01);
+            ld2(beta + (kk + 1) * LDR + c0, b10, b11);
+            cfms(o0, v0, b00);
+            cfms(o1, v0, b01);
+            cfms(o0, v1, b10);
+            cfms(o1, v1, b11);
+          }
         }
-        C* up = u + (long long)(d.wlo + p - 1) * rs + (long long)j * a.R + r;
-        *up = (a.mode == 0) ? o : csub(*up, o);
+        C* up = u + (long long)(d.wlo + p - 1) * rs + (long long)j * a.R + rbase + c0;
+        if (valid[0]) up[0] = bwd ? csub(uo[0][i], o0) : o0;
+        if (valid[1]) up[1] = bwd ? csub(uo[1][i], o1) : o1;
       }
     }
-    allgather<R, W, T>(xown, xnext);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) set_status(a.status, HS_ETIMEOUT, front, j);
-      drain_inflight(bars, t, ncol, a.spin);
-      return;
-    }
-    if (tid == 0 && t + 2 < ncol) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&bars[b], pbytes);
-      tma_bulk_g2s(b ? buf1 : buf0, fac + (long long)(j - 2) * pe, pbytes, &bars[b]);
+  };
+  C o0[RPT][ROWS], o1[RPT][ROWS];
+  load_old(o0, rgt);
+  if (ncol > 1) load_old(o1, rgt - 1);
+  for (int t = 0; t < ncol; t += 2) {
+    step(t, o0);
+    if (!ok) break;
+    if (t + 2 < ncol) load_old(o0, rgt - t - 2);
+    if (t + 1 < ncol) {
+      step(t + 1, o1);
+      if (!ok) break;
+      if (t + 3 < ncol) load_old(o1, rgt - t - 3);
     }
   }
-  if (has_right && valid) {
-    const int s = rgt + 1;
+  if (!ok) {
+    if ((tid & 31) == 0) set_status(a.status, HS_ETIMEOUT, front, rgt);
+    return;
+  }
+  consumer_barrier(NCONS);
+  if (tid == 0) mbar_arrive(&empty[(ncol - 1) % S13]);
+  if (has_right) {
+    const int sc = rgt + 1;
 #pragma unroll
-    for (int q = 0; q < ROWS; ++q) {
-      const int p = sl * ROWS + q;
-      if (p >= d.out_off && p < d.out_off + d.d_out) {
-        C o = xsb[((fb + k) * a.R + r) * W + p];
-        C* up = u + (long long)(d.wlo + p - 1) * rs + (long long)s * a.R + r;
-        *up = (a.mode == 0) ? o : csub(*up, o);
+    for (int i = 0; i < ROWS; ++i)
+      if (isout[i]) {
+        const int p = rg + NRG * i;
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+          if (valid[q]) {
+            const C o = xsb[((fb + k) * a.R + rr[q]) * W + p];
+            C* up = u + (long long)(d.wlo + p - 1) * rs + (long long)sc * a.R + rbase + c0 + q;
+            *up = bwd ? csub(*up, o) : o;
+          }
       }
-    }
   }
 }
 
 template <typename R, int W>
 int run_stage_w(const Plan& p, SweepArgs a, cudaStream_t s) {
-  constexpr int T = TPR<W>::value;
-  constexpr int RT = NT / T;
-  int dmax = std::max(a.blk[0].d_out, a.nfront > 1 ? a.blk[1].d_out : 0);
-  const size_t sm13 = ChunkSmem<R, W>::bytes(dmax);
+  using TL = Tile13<R, W>;
+  const int dmax = std::max(a.blk[0].d_out, a.nfront > 1 ? a.blk[1].d_out : 0);
+  const size_t sm1 = tile_smem<R, W>(dmax, false);
+  const size_t sm3 = tile_smem<R, W>(dmax, true);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(phase1_kernel<R, W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-    cudaFuncSetAttribute(phase3_kernel<R, W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-    cudaFuncSetAttribute(phase2_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    cudaFuncSetAttribute(phase1_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(phase3_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(phase2_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
-  dim3 g13(a.P, (a.R + RT - 1) / RT, a.nfront);
+  if (sm1 > 220 * 1024 || sm3 > 220 * 1024 || phase2_smem<R, W>(a.P - 1) > 220 * 1024) return HS_EUNSUPPORTED;
+  dim3 g13(a.P, (a.R + TL::RG - 1) / TL::RG, a.nfront);
   note_launch();
-  phase1_kernel<R, W, T><<<g13, NT, sm13, s>>>(a);
+  phase1_kernel<R, W><<<g13, TL::NCONS + 32, sm1, s>>>(a);
   if (a.P > 1) {
-    const size_t sm2 = 128 + 2 * (((size_t)red_elems(W) * sizeof(cplx<R>) + 127) / 128 * 128);
-    dim3 g2(1, (a.R + NT / 32 - 1) / (NT / 32), a.nfront);
+    dim3 g2(1, (a.R + WPC - 1) / WPC, a.nfront);
     note_launch();
-    phase2_kernel<R, W><<<g2, NT, sm2, s>>>(a);
+    phase2_kernel<R, W><<<g2, NT + 32, phase2_smem<R, W>(a.P - 1), s>>>(a);
   }
   note_launch();
-  phase3_kernel<R, W, T><<<g13, NT, sm13, s>>>(a);
+  phase3_kernel<R, W><<<g13, TL::NCONS + 32, sm3, s>>>(a);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HS_OK : cuda_status(e);
 }
