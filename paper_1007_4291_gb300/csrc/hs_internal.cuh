@@ -87,6 +87,10 @@ struct Plan {
   double* d_m0 = nullptr;   // omega^2 / c^2 per point
   float* f_m0 = nullptr;
   double* d_cinv2 = nullptr; // 1/c^2 per point
+  // double-float copies for the Krylov solver of the complex64 path:
+  // 1D tables as complex double-float, omega^2/c^2 per point as double-float
+  void* k_inv_s1 = nullptr; void* k_a1 = nullptr; void* k_inv_s2 = nullptr; void* k_a2 = nullptr;
+  void* k_m0 = nullptr;
   c128* d_s2win = nullptr;  // per-block window tables: 1/s2B(p), s2B(p+1/2)/h^2, s2B(p-1/2)/h^2
   BlockDesc* d_blocks = nullptr;
   void* d_fac = nullptr;    long long fac_elems = 0;   // factor payloads (c64 or c128 elements)
@@ -101,11 +105,6 @@ struct Plan {
   void* d_ps = nullptr;     // separator forward values psi
   int* d_status = nullptr;  // device status word(s): [0] code, [1] block, [2] column
   long long bytes = 0;
-  // Krylov workspace, carved from the process-wide pool for the duration of hs_solve
-  c128* d_V = nullptr; c64* d_Zk = nullptr; c128* d_x = nullptr; c128* d_f = nullptr;
-  c128* d_part = nullptr; c128* d_h = nullptr; double* d_nrm = nullptr;
-  int kry_m = 0, kry_R = 0;
-  long long kry_bytes = 0;
 };
 
 // ---------------------------------------------------------------- helpers

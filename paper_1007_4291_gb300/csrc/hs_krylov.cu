@@ -1,11 +1,19 @@
 // Outer Krylov solver of Sec. 2.3: GMRES preconditioned by the sweep M_alpha.
 // Implemented as right-preconditioned flexible GMRES(m): z_j = M_alpha v_j in
-// the factor precision, w = A z_j in FP64, classical Gram-Schmidt in FP64 with
-// a second pass when the norm drops below 1/sqrt(2) of its value (DGKS),
-// Givens rotations on the host, and the FP64 true residual ||f - A u|| at
-// every restart.  All right-hand sides advance in lock step; a right-hand
-// side that has converged at the start of a cycle is carried with a zero
-// basis vector and receives no update.
+// the factor precision, w = A z_j, classical Gram-Schmidt (optionally with a
+// second pass when the norm drops below 1/sqrt(2) of its value, DGKS),
+// Givens rotations on the host, and the true residual ||f - A u|| at every
+// restart.  All right-hand sides advance in lock step; a right-hand side that
+// has converged at the start of a cycle is carried with a zero basis vector
+// and receives no update.
+//
+// Two arithmetics for the Arnoldi vectors, the iterate and the residual:
+//  * complex128 factors: native FP64 (the plain double-precision solver);
+//  * complex64 factors: double-float (two floats per real, 48-bit
+//    significand, see hs_df64.cuh) on the FP32 pipes, because GB300 runs
+//    FP64 at 1/64 of its FP32 rate and these kernels would otherwise be
+//    FP64-ALU-bound instead of memory-bound.
+// The preconditioned vectors z_j are stored in the factor precision.
 //
 // Vectors inside the solver use the RHS-inner layout [point][rhs].
 #include <algorithm>
@@ -13,18 +21,78 @@
 #include <cmath>
 #include <complex>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 #include "hs_internal.cuh"
+#include "hs_df64.cuh"
 
 namespace hs {
 namespace {
 
 constexpr int KT = 256;  // threads per CTA: 8 warps x 32 RHS lanes
 
-// part[cta][i][r] = sum over this CTA's points of conj(V_i) w ; slot i = nv holds |w|^2.
-template <int MAXJ>
-__global__ void __launch_bounds__(KT) dots_kernel(const c128* __restrict__ V, long long vstride, int nv,
-                                                  const c128* __restrict__ w, long long npts, int R,
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return sms;
+}
+
+// ---------------------------------------------------------------- arithmetic
+// Element operations of the two solver arithmetics.
+struct F64 {
+  using V = c128;    // Krylov vector element
+  using A = c128;    // dot-product accumulator
+  using N = double;  // norm accumulator
+  static __device__ __forceinline__ A zero() { return c128{0, 0}; }
+  static __device__ __forceinline__ void acc_conj(A& acc, V v, V w) { cfmaconj(acc, v, w); }
+  static __device__ __forceinline__ void norm_zero(N& n) { n = 0.0; }
+  static __device__ __forceinline__ void norm_acc(N& nrm, V w) { nrm = fma(w.re, w.re, fma(w.im, w.im, nrm)); }
+  static __device__ __forceinline__ double norm_out(N n) { return n; }
+  static __device__ __forceinline__ c128 to_c128(A a) { return a; }
+  static __device__ __forceinline__ V coef(c128 h) { return h; }
+  static __device__ __forceinline__ void sub_prod(V& w, V h, V v) { cfms(w, h, v); }
+  template <typename ZT>
+  static __device__ __forceinline__ void add_prod_z(V& x, V y, cplx<ZT> z) {
+    cfma(x, y, c128{(double)z.re, (double)z.im});
+  }
+  static __device__ __forceinline__ c64 to_c64(V v) { return c64{(float)v.re, (float)v.im}; }
+  static __device__ __forceinline__ V from_c128(c128 v) { return v; }
+  static __device__ __forceinline__ c128 out_c128(V v) { return v; }
+};
+
+struct DF64 {
+  using V = cdf;
+  using A = cdf;
+  using N = df;
+  static __device__ __forceinline__ A zero() { return cdf{df{0.f, 0.f}, df{0.f, 0.f}}; }
+  static __device__ __forceinline__ void acc_conj(A& acc, V v, V w) { cdf_fma_conj(acc, v, w); }
+  static __device__ __forceinline__ void norm_zero(N& n) { n = df{0.f, 0.f}; }
+  static __device__ __forceinline__ void norm_acc(N& nrm, V w) {
+    df_fma(nrm, w.re, w.re);
+    df_fma(nrm, w.im, w.im);
+  }
+  static __device__ __forceinline__ double norm_out(N n) { return df_to_double(n); }
+  static __device__ __forceinline__ c128 to_c128(A a) { return cdf_to_c128(a); }
+  static __device__ __forceinline__ V coef(c128 h) { return cdf_from_c128(h); }
+  static __device__ __forceinline__ void sub_prod(V& w, V h, V v) { cdf_fms(w, h, v); }
+  template <typename ZT>
+  static __device__ __forceinline__ void add_prod_z(V& x, V y, cplx<ZT> z) {
+    cdf_fma_c64(x, y, c64{(float)z.re, (float)z.im});
+  }
+  static __device__ __forceinline__ c64 to_c64(V v) { return c64{v.re.h, v.im.h}; }
+  static __device__ __forceinline__ V from_c128(c128 v) { return cdf_from_c128(v); }
+  static __device__ __forceinline__ c128 out_c128(V v) { return cdf_to_c128(v); }
+};
+
+// ---------------------------------------------------------------- kernels
+// part[cta][i][r] = sum over this CTA's points of conj(V_i) w ; slot nv holds |w|^2.
+template <typename AR, int MAXJ>
+__global__ void __launch_bounds__(KT) dots_kernel(const typename AR::V* __restrict__ V, long long vstride, int nv,
+                                                  const typename AR::V* __restrict__ w, long long npts, int R,
                                                   c128* __restrict__ part) {
   __shared__ double sre[MAXJ + 1][32], sim[MAXJ + 1][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -34,28 +102,30 @@ __global__ void __launch_bounds__(KT) dots_kernel(const c128* __restrict__ V, lo
     sim[t / 32][t % 32] = 0.0;
   }
   __syncthreads();
-  c128 acc[MAXJ];
+  typename AR::A acc[MAXJ];
 #pragma unroll
-  for (int i = 0; i < MAXJ; ++i) acc[i] = c128{0, 0};
-  double nrm = 0.0;
+  for (int i = 0; i < MAXJ; ++i) acc[i] = AR::zero();
+  typename AR::N nrm;
+  AR::norm_zero(nrm);
   if (r < R) {
     for (long long pt = (long long)blockIdx.x * 8 + warp; pt < npts; pt += (long long)gridDim.x * 8) {
       const long long e = pt * R + r;
-      const c128 wv = w[e];
-      nrm = fma(wv.re, wv.re, fma(wv.im, wv.im, nrm));
+      const typename AR::V wv = w[e];
+      AR::norm_acc(nrm, wv);
 #pragma unroll
       for (int i = 0; i < MAXJ; ++i)
-        if (i < nv) cfmaconj(acc[i], V[i * vstride + e], wv);
+        if (i < nv) AR::acc_conj(acc[i], V[i * vstride + e], wv);
     }
   }
 #pragma unroll
   for (int i = 0; i < MAXJ; ++i) {
     if (i < nv) {
-      atomicAdd(&sre[i][lane], acc[i].re);
-      atomicAdd(&sim[i][lane], acc[i].im);
+      const c128 a = AR::to_c128(acc[i]);
+      atomicAdd(&sre[i][lane], a.re);
+      atomicAdd(&sim[i][lane], a.im);
     }
   }
-  atomicAdd(&sre[MAXJ][lane], nrm);
+  atomicAdd(&sre[MAXJ][lane], AR::norm_out(nrm));
   __syncthreads();
   const long long cta = blockIdx.x;
   for (int t = threadIdx.x; t < (nv + 1) * 32; t += KT) {
@@ -77,145 +147,181 @@ __global__ void reduce_parts_kernel(const c128* __restrict__ part, int nctas, in
   out[i * R + r] = s;
 }
 
-// w -= sum_i h[i][r] V_i ; part[cta][0][r] = partial |w_new|^2
-template <int MAXJ>
-__global__ void __launch_bounds__(KT) update_kernel(const c128* __restrict__ V, long long vstride, int nv,
-                                                    const c128* __restrict__ h, c128* __restrict__ w,
+// w -= sum_i h[i][r] V_i ; part[cta][r] = partial |w_new|^2
+template <typename AR, int MAXJ>
+__global__ void __launch_bounds__(KT) update_kernel(const typename AR::V* __restrict__ V, long long vstride, int nv,
+                                                    const c128* __restrict__ h, typename AR::V* __restrict__ w,
                                                     long long npts, int R, c128* __restrict__ part) {
   __shared__ double snrm[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = blockIdx.y * 32 + lane;
   if (threadIdx.x < 32) snrm[threadIdx.x] = 0.0;
   __syncthreads();
-  c128 hc[MAXJ];
+  typename AR::V hc[MAXJ];
 #pragma unroll
-  for (int i = 0; i < MAXJ; ++i) hc[i] = (i < nv && r < R) ? h[i * R + r] : c128{0, 0};
-  double nrm = 0.0;
+  for (int i = 0; i < MAXJ; ++i) hc[i] = AR::coef((i < nv && r < R) ? h[i * R + r] : c128{0, 0});
+  typename AR::N nrm;
+  AR::norm_zero(nrm);
   if (r < R) {
     for (long long pt = (long long)blockIdx.x * 8 + warp; pt < npts; pt += (long long)gridDim.x * 8) {
       const long long e = pt * R + r;
-      c128 wv = w[e];
+      typename AR::V wv = w[e];
 #pragma unroll
       for (int i = 0; i < MAXJ; ++i)
-        if (i < nv) cfms(wv, hc[i], V[i * vstride + e]);
+        if (i < nv) AR::sub_prod(wv, hc[i], V[i * vstride + e]);
       w[e] = wv;
-      nrm = fma(wv.re, wv.re, fma(wv.im, wv.im, nrm));
+      AR::norm_acc(nrm, wv);
     }
   }
-  atomicAdd(&snrm[lane], nrm);
+  atomicAdd(&snrm[lane], AR::norm_out(nrm));
   __syncthreads();
   const int rr = blockIdx.y * 32 + threadIdx.x;
   if (threadIdx.x < 32 && rr < R) part[(long long)blockIdx.x * R + rr] = c128{snrm[threadIdx.x], 0.0};
 }
 
-// v = w * s[r]  (c128), or z = (c64) v
-__global__ void scale_kernel(const c128* __restrict__ w, const double* __restrict__ s, c128* __restrict__ v,
-                             long long total, int R) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+// v = w * s[r]
+__global__ void scale_f64_kernel(const c128* __restrict__ w, const double* __restrict__ s, c128* __restrict__ v,
+                                 long long total, int R) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
     const double f = s[e % R];
     v[e] = c128{w[e].re * f, w[e].im * f};
   }
 }
-__global__ void to_c64_kernel(const c128* __restrict__ v, c64* __restrict__ z, long long total) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x)
-    z[e] = c64{(float)v[e].re, (float)v[e].im};
+__global__ void scale_df_kernel(const cdf* __restrict__ w, const df* __restrict__ s, cdf* __restrict__ v,
+                                long long total, int R) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    v[e] = cdf_scale(w[e], s[e % R]);
+}
+template <typename AR>
+__global__ void to_c64_kernel(const typename AR::V* __restrict__ v, c64* __restrict__ z, long long total) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    z[e] = AR::to_c64(v[e]);
 }
 
 // x += sum_i y[i][r] Z_i
-template <int MAXJ, typename ZT>
+template <typename AR, int MAXJ, typename ZT>
 __global__ void __launch_bounds__(KT) xupdate_kernel(const cplx<ZT>* __restrict__ Z, long long zstride, int k,
-                                                     const c128* __restrict__ y, c128* __restrict__ x,
+                                                     const c128* __restrict__ y, typename AR::V* __restrict__ x,
                                                      long long npts, int R) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = blockIdx.y * 32 + lane;
   if (r >= R) return;
-  c128 yc[MAXJ];
+  typename AR::V yc[MAXJ];
 #pragma unroll
-  for (int i = 0; i < MAXJ; ++i) yc[i] = (i < k) ? y[i * R + r] : c128{0, 0};
+  for (int i = 0; i < MAXJ; ++i) yc[i] = AR::coef((i < k) ? y[i * R + r] : c128{0, 0});
   for (long long pt = (long long)blockIdx.x * 8 + warp; pt < npts; pt += (long long)gridDim.x * 8) {
     const long long e = pt * R + r;
-    c128 xv = x[e];
+    typename AR::V xv = x[e];
 #pragma unroll
     for (int i = 0; i < MAXJ; ++i)
-      if (i < k) {
-        const cplx<ZT> zv = Z[i * zstride + e];
-        cfma(xv, yc[i], c128{(double)zv.re, (double)zv.im});
-      }
+      if (i < k) AR::add_prod_z(xv, yc[i], Z[i * zstride + e]);
     x[e] = xv;
   }
 }
 
-int sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+// Layout conversion ABI [rhs][point] (complex128) <-> solver [point][rhs] (V).
+template <typename AR, bool TO_INTERNAL>
+__global__ void relayout_v_kernel(const void* __restrict__ srcv, void* __restrict__ dstv, long long npts, int R) {
+  using V = typename AR::V;
+  __shared__ V tile[32][33];
+  const long long p0 = (long long)blockIdx.x * 32;
+  const int r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int yy = ty; yy < 32; yy += 8) {
+    if (TO_INTERNAL) {
+      const c128* src = reinterpret_cast<const c128*>(srcv);
+      const long long pt = p0 + tx;
+      const int r = r0 + yy;
+      if (pt < npts && r < R) tile[yy][tx] = AR::from_c128(src[(long long)r * npts + pt]);
+    } else {
+      const V* src = reinterpret_cast<const V*>(srcv);
+      const long long pt = p0 + yy;
+      const int r = r0 + tx;
+      if (pt < npts && r < R) tile[yy][tx] = src[pt * R + r];
+    }
   }
-  return sms;
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    if (TO_INTERNAL) {
+      V* dst = reinterpret_cast<V*>(dstv);
+      const long long pt = p0 + yy;
+      const int r = r0 + tx;
+      if (pt < npts && r < R) dst[pt * R + r] = tile[tx][yy];
+    } else {
+      c128* dst = reinterpret_cast<c128*>(dstv);
+      const long long pt = p0 + tx;
+      const int r = r0 + yy;
+      if (pt < npts && r < R) dst[(long long)r * npts + pt] = AR::out_c128(tile[tx][yy]);
+    }
+  }
 }
 
-struct Kry {
-  Plan& p;
-  int R;
-  long long npts, vstride;
-  cudaStream_t s;
-  int nctas;
-  dim3 grid() const { return dim3(nctas, (R + 31) / 32); }
-
-  // h[i][r] (i < nv) and |w|^2 (slot nv) into p.d_h
-  void dots(const c128* V, int nv, const c128* w) {
-    const dim3 g = grid();
-    note_launch();
-    if (nv <= 8) dots_kernel<8><<<g, KT, 0, s>>>(V, vstride, nv, w, npts, R, p.d_part);
-    else if (nv <= 16) dots_kernel<16><<<g, KT, 0, s>>>(V, vstride, nv, w, npts, R, p.d_part);
-    else dots_kernel<32><<<g, KT, 0, s>>>(V, vstride, nv, w, npts, R, p.d_part);
-    const int mj = (nv <= 8) ? 8 : (nv <= 16) ? 16 : 32;
-    const int tot = (nv + 1) * R;
-    note_launch();
-    reduce_parts_kernel<<<(tot + 255) / 256, 256, 0, s>>>(p.d_part, nctas, mj + 1, nv + 1, R, p.d_h);
-  }
-  // w -= V h ; |w|^2 -> p.d_h row `slot`
-  void update(const c128* V, int nv, const c128* h, c128* w, int slot) {
-    const dim3 g = grid();
-    note_launch();
-    if (nv <= 8) update_kernel<8><<<g, KT, 0, s>>>(V, vstride, nv, h, w, npts, R, p.d_part);
-    else if (nv <= 16) update_kernel<16><<<g, KT, 0, s>>>(V, vstride, nv, h, w, npts, R, p.d_part);
-    else update_kernel<32><<<g, KT, 0, s>>>(V, vstride, nv, h, w, npts, R, p.d_part);
-    note_launch();
-    reduce_parts_kernel<<<(R + 255) / 256, 256, 0, s>>>(p.d_part, nctas, 1, 1, R, p.d_h + (long long)slot * R);
-  }
-  void norm2(const c128* w, int slot) {
-    note_launch();
-    dots_kernel<8><<<grid(), KT, 0, s>>>(nullptr, vstride, 0, w, npts, R, p.d_part);
-    note_launch();
-    reduce_parts_kernel<<<(R + 255) / 256, 256, 0, s>>>(p.d_part, nctas, 9, 1, R, p.d_h + (long long)slot * R);
-  }
-  void scale(const c128* w, const std::vector<double>& f, c128* v) {
-    cudaMemcpyAsync(p.d_nrm, f.data(), R * sizeof(double), cudaMemcpyHostToDevice, s);
-    note_launch();
-    scale_kernel<<<sm_count() * 8, 256, 0, s>>>(w, p.d_nrm, v, npts * R, R);
-  }
-  template <typename ZT>
-  void xupdate(const cplx<ZT>* Z, int k, const c128* y, c128* x) {
-    const dim3 g = grid();
-    note_launch();
-    if (k <= 8) xupdate_kernel<8, ZT><<<g, KT, 0, s>>>(Z, vstride, k, y, x, npts, R);
-    else if (k <= 16) xupdate_kernel<16, ZT><<<g, KT, 0, s>>>(Z, vstride, k, y, x, npts, R);
-    else xupdate_kernel<32, ZT><<<g, KT, 0, s>>>(Z, vstride, k, y, x, npts, R);
-  }
+// Eq. helmd in double-float: y = A x (x complex float or double-float), or
+// y = f - A x.  Interior points use the real form (sum of the four
+// neighbours)(n+1)^2 + (omega^2/c^2 - 4(n+1)^2) x; PML points the complex
+// coefficients built from the double-float stretch tables.
+struct DfTabs {
+  const cdf* inv_s1; const cdf* a1; const cdf* inv_s2; const cdf* a2;
+  const df* m0; const unsigned char* pml1; const unsigned char* pml2;
+  float ih2;   // (n+1)^2, exact in FP32 for n < 4095
 };
 
-using zc = std::complex<double>;
-
-void givens(zc a, zc b, double& c, zc& s) {
-  if (b == 0.0) { c = 1.0; s = 0.0; return; }
-  if (a == 0.0) { c = 0.0; s = std::conj(b) / std::abs(b); return; }
-  const double na = std::hypot(std::abs(a), std::abs(b));
-  c = std::abs(a) / na;
-  s = (a / std::abs(a)) * std::conj(b) / na;
+template <bool XDF>
+__device__ __forceinline__ cdf ld_x(const void* x, long long k) {
+  if (XDF) return reinterpret_cast<const cdf*>(x)[k];
+  const c64 v = reinterpret_cast<const c64*>(x)[k];
+  return cdf{df{v.re, 0.f}, df{v.im, 0.f}};
 }
 
+template <bool XDF, bool RESID>
+__global__ void __launch_bounds__(256) matvec_df_kernel(const void* __restrict__ x, cdf* __restrict__ y,
+                                                        const cdf* __restrict__ f, DfTabs t, int n, int R) {
+  const long long n2 = (long long)n * n;
+  const long long total = n2 * R;
+  const cdf zero{df{0.f, 0.f}, df{0.f, 0.f}};
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long pt = e / R;
+    const int j = (int)(pt / n), i = (int)(pt - (long long)j * n);
+    const long long sx = R, sy = (long long)n * R;
+    const cdf xc = ld_x<XDF>(x, e);
+    const cdf xe = (i + 1 < n) ? ld_x<XDF>(x, e + sx) : zero;
+    const cdf xw = (i > 0) ? ld_x<XDF>(x, e - sx) : zero;
+    const cdf xn = (j + 1 < n) ? ld_x<XDF>(x, e + sy) : zero;
+    const cdf xs = (j > 0) ? ld_x<XDF>(x, e - sy) : zero;
+    const df m0 = t.m0[pt];
+    cdf acc;
+    if (!t.pml1[i + 1] && !t.pml2[j + 1]) {
+      const df dg = df_add(m0, df{-4.f * t.ih2, 0.f});
+      const cdf s4 = cdf_add(cdf_add(xe, xw), cdf_add(xn, xs));
+      acc.re = df_add(df_mul_f(s4.re, t.ih2), df_mul(dg, xc.re));
+      acc.im = df_add(df_mul_f(s4.im, t.ih2), df_mul(dg, xc.im));
+    } else {
+      const cdf is1 = t.inv_s1[i + 1], is2 = t.inv_s2[j + 1];
+      const cdf E = cdf_mul(t.a1[i + 1], is2), Wc = cdf_mul(t.a1[i], is2);
+      const cdf N = cdf_mul(t.a2[j + 1], is1), S = cdf_mul(t.a2[j], is1);
+      const cdf ss = cdf_mul(is1, is2);
+      const cdf D = cdf_sub(cdf{df_mul(ss.re, m0), df_mul(ss.im, m0)}, cdf_add(cdf_add(E, Wc), cdf_add(N, S)));
+      acc = cdf_mul(D, xc);
+      acc = cdf_add(acc, cdf_mul(E, xe));
+      acc = cdf_add(acc, cdf_mul(Wc, xw));
+      acc = cdf_add(acc, cdf_mul(N, xn));
+      acc = cdf_add(acc, cdf_mul(S, xs));
+    }
+    y[e] = RESID ? cdf_sub(f[e], acc) : acc;
+  }
+}
+
+int grid1(long long total) {
+  long long g = (total + 255) / 256;
+  long long cap = (long long)sm_count() * 32;
+  return (int)(g < cap ? g : cap);
+}
+
+// ---------------------------------------------------------------- workspace
 // Process-wide Krylov workspace: one device allocation reused by every
 // hs_solve (held under a mutex for the duration of a solve, so concurrent
 // solves from several host threads serialise instead of racing).  It grows
@@ -232,13 +338,24 @@ KrylovPool& pool() {
 
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
-int carve_workspace(Plan& p, int m, int R) {
+struct Work {
+  void* V;      // (m+1) Arnoldi vectors (c128 or cdf, 16 bytes per element)
+  void* Z;      // m preconditioned vectors (factor precision)
+  void* x;      // iterate
+  void* f;      // right-hand side
+  c128* part;   // CTA partial sums
+  c128* h;      // small coefficient vectors (34 rows of R)
+  void* s;      // per-RHS scale factors (double or double-float)
+};
+
+int carve_workspace(const Plan& p, int m, int R, Work& w) {
   KrylovPool& kp = pool();
+  const size_t ves = 16;
   const size_t zes = (p.prec == HS_C64) ? sizeof(c64) : sizeof(c128);
   const size_t npts = (size_t)p.n * p.n, vs = npts * R;
   const size_t nct = (size_t)sm_count() * 2;
-  const size_t b1 = al256((m + 1) * vs * sizeof(c128)), b2 = al256(m * vs * zes), b3 = al256(vs * sizeof(c128));
-  const size_t b4 = al256(nct * 33 * R * sizeof(c128)), b5 = al256(34 * R * sizeof(c128)), b6 = al256(R * sizeof(double));
+  const size_t b1 = al256((m + 1) * vs * ves), b2 = al256(m * vs * zes), b3 = al256(vs * ves);
+  const size_t b4 = al256(nct * 33 * R * sizeof(c128)), b5 = al256(34 * R * sizeof(c128)), b6 = al256(R * 8);
   const size_t need = b1 + b2 + 2 * b3 + b4 + b5 + b6;
   if (kp.bytes < need) {
     if (kp.base) cudaFree(kp.base);
@@ -252,56 +369,153 @@ int carve_workspace(Plan& p, int m, int R) {
     kp.bytes = need;
   }
   char* q = kp.base;
-  p.d_V = (c128*)q; q += b1;
-  p.d_Zk = (c64*)q; q += b2;
-  p.d_x = (c128*)q; q += b3;
-  p.d_f = (c128*)q; q += b3;
-  p.d_part = (c128*)q; q += b4;
-  p.d_h = (c128*)q; q += b5;
-  p.d_nrm = (double*)q;
-  p.kry_m = m; p.kry_R = R;
-  p.kry_bytes = (long long)need;
+  w.V = q; q += b1;
+  w.Z = q; q += b2;
+  w.x = q; q += b3;
+  w.f = q; q += b3;
+  w.part = (c128*)q; q += b4;
+  w.h = (c128*)q; q += b5;
+  w.s = q;
   return HS_OK;
 }
 
-}  // namespace
-}  // namespace hs
+using zc = std::complex<double>;
 
-using namespace hs;
+void givens(zc a, zc b, double& c, zc& s) {
+  if (b == 0.0) { c = 1.0; s = 0.0; return; }
+  if (a == 0.0) { c = 0.0; s = std::conj(b) / std::abs(b); return; }
+  const double na = std::hypot(std::abs(a), std::abs(b));
+  c = std::abs(a) / na;
+  s = (a / std::abs(a)) * std::conj(b) / na;
+}
 
-extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double tol, int maxit,
-                        hs_solve_info* info, void* stream) {
-  if (!plan || !f || !u || !(tol > 0.0) || maxit < 1) return HS_EINVAL;
-  Plan& p = *reinterpret_cast<Plan*>(plan);
-  if (nrhs < 1 || nrhs > p.max_nrhs) return HS_EINVAL;
+// ---------------------------------------------------------------- solver
+template <typename AR>
+struct Solver {
+  using V = typename AR::V;
+  Plan& p;
+  int R;
+  long long npts, vs;
+  cudaStream_t s;
+  Work w;
+  int nctas;
+  std::vector<float> scratch;   // host staging for double-float scale factors
+  dim3 grid() const { return dim3(nctas, (R + 31) / 32); }
+
+  // h[i][r] (i < nv) and |v|^2 (slot nv) into w.h
+  void dots(const V* Vb, int nv, const V* v) {
+    const dim3 g = grid();
+    note_launch();
+    if (nv <= 8) dots_kernel<AR, 8><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
+    else if (nv <= 16) dots_kernel<AR, 16><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
+    else dots_kernel<AR, 32><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
+    const int mj = (nv <= 8) ? 8 : (nv <= 16) ? 16 : 32;
+    note_launch();
+    reduce_parts_kernel<<<((nv + 1) * R + 255) / 256, 256, 0, s>>>(w.part, nctas, mj + 1, nv + 1, R, w.h);
+  }
+  // v -= V h ; |v|^2 -> w.h row `slot`
+  void update(const V* Vb, int nv, V* v, int slot) {
+    const dim3 g = grid();
+    note_launch();
+    if (nv <= 8) update_kernel<AR, 8><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part);
+    else if (nv <= 16) update_kernel<AR, 16><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part);
+    else update_kernel<AR, 32><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part);
+    note_launch();
+    reduce_parts_kernel<<<(R + 255) / 256, 256, 0, s>>>(w.part, nctas, 1, 1, R, w.h + (long long)slot * R);
+  }
+  void norm2(const V* v, int slot) {
+    note_launch();
+    dots_kernel<AR, 8><<<grid(), KT, 0, s>>>(nullptr, vs, 0, v, npts, R, w.part);
+    note_launch();
+    reduce_parts_kernel<<<(R + 255) / 256, 256, 0, s>>>(w.part, nctas, 9, 1, R, w.h + (long long)slot * R);
+  }
+  // dst = src * f[r]; the host factors are copied synchronously (tiny)
+  void scale(const V* src, const std::vector<double>& f, V* dst) {
+    note_launch();
+    if constexpr (std::is_same<AR, F64>::value) {
+      cudaMemcpyAsync(w.s, f.data(), R * sizeof(double), cudaMemcpyHostToDevice, s);
+      cudaStreamSynchronize(s);
+      scale_f64_kernel<<<sm_count() * 8, 256, 0, s>>>(src, (const double*)w.s, dst, vs, R);
+    } else {
+      scratch.resize(2 * R);
+      for (int r = 0; r < R; ++r) {
+        scratch[2 * r] = (float)f[r];
+        scratch[2 * r + 1] = (float)(f[r] - (double)scratch[2 * r]);
+      }
+      cudaMemcpyAsync(w.s, scratch.data(), 2 * R * sizeof(float), cudaMemcpyHostToDevice, s);
+      cudaStreamSynchronize(s);
+      scale_df_kernel<<<sm_count() * 8, 256, 0, s>>>(src, (const df*)w.s, dst, vs, R);
+    }
+  }
+  template <typename ZT>
+  void xupdate(const cplx<ZT>* Z, int k, V* x) {
+    const dim3 g = grid();
+    note_launch();
+    if (k <= 8) xupdate_kernel<AR, 8, ZT><<<g, KT, 0, s>>>(Z, vs, k, w.h, x, npts, R);
+    else if (k <= 16) xupdate_kernel<AR, 16, ZT><<<g, KT, 0, s>>>(Z, vs, k, w.h, x, npts, R);
+    else xupdate_kernel<AR, 32, ZT><<<g, KT, 0, s>>>(Z, vs, k, w.h, x, npts, R);
+  }
+  // y = A x, or y = f - A x when f is given.  x is a solver vector
+  // (solver_vec) or a preconditioned vector in the factor precision.
+  void matvec(const void* x, bool solver_vec, V* y, const V* f) {
+    if constexpr (std::is_same<AR, F64>::value) {
+      matvec_internal_f64(p, x, false, y, f, R, s);
+      (void)solver_vec;
+    } else {
+      DfTabs t{(const cdf*)p.k_inv_s1, (const cdf*)p.k_a1, (const cdf*)p.k_inv_s2, (const cdf*)p.k_a2,
+               (const df*)p.k_m0, p.d_pml1, p.d_pml2, (float)((double)(p.n + 1) * (p.n + 1))};
+      const int g = grid1(vs);
+      note_launch();
+      if (solver_vec) {
+        if (f) matvec_df_kernel<true, true><<<g, 256, 0, s>>>(x, y, f, t, p.n, R);
+        else matvec_df_kernel<true, false><<<g, 256, 0, s>>>(x, y, f, t, p.n, R);
+      } else {
+        if (f) matvec_df_kernel<false, true><<<g, 256, 0, s>>>(x, y, f, t, p.n, R);
+        else matvec_df_kernel<false, false><<<g, 256, 0, s>>>(x, y, f, t, p.n, R);
+      }
+    }
+  }
+  void to_c64(const V* v, c64* z) {
+    note_launch();
+    to_c64_kernel<AR><<<sm_count() * 8, 256, 0, s>>>(v, z, vs);
+  }
+  void relayout(const void* src, void* dst, bool to_internal) {
+    dim3 gr((unsigned)((npts + 31) / 32), (R + 31) / 32);
+    note_launch();
+    if (to_internal) relayout_v_kernel<AR, true><<<gr, dim3(32, 8), 0, s>>>(src, dst, npts, R);
+    else relayout_v_kernel<AR, false><<<gr, dim3(32, 8), 0, s>>>(src, dst, npts, R);
+  }
+};
+
+template <typename AR>
+int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs_solve_info* info, cudaStream_t s) {
+  using V = typename AR::V;
   const auto t0 = std::chrono::steady_clock::now();
-  cudaStream_t s = (cudaStream_t)stream;
   const int R = nrhs;
   const int m = std::min(std::max(p.opt.restart, 1), 32);
   std::lock_guard<std::mutex> guard(pool().mu);
-  int st = carve_workspace(p, m, R);
+  Solver<AR> K{p, R, (long long)p.n * p.n, (long long)p.n * p.n * R, s, Work{}, sm_count() * 2, {}};
+  int st = carve_workspace(p, m, R, K.w);
   if (st != HS_OK) return st;
-  const long long npts = (long long)p.n * p.n, vs = npts * R;
-  Kry K{p, R, npts, vs, s, sm_count() * 2};
-  c128* V = p.d_V;
-  c64* Z = p.d_Zk;                       // c64 basis (factor precision c64)
-  c128* Z2 = reinterpret_cast<c128*>(p.d_Zk);  // c128 basis (factor precision c128)
-  c128* x = p.d_x;
-  c128* fi = p.d_f;
-  if ((st = layout_to_internal(f, HS_C128, fi, HS_C128, (int)npts, R, s)) != HS_OK) return st;
-  if ((st = layout_to_internal(u, HS_C128, x, HS_C128, (int)npts, R, s)) != HS_OK) return st;
+  const long long vs = K.vs;
+  V* Vb = (V*)K.w.V;
+  V* x = (V*)K.w.x;
+  V* fi = (V*)K.w.f;
+  c64* Z = (c64*)K.w.Z;                      // complex64 factors: preconditioned vectors in c64
+  c128* Z2 = (c128*)K.w.Z;                   // complex128 factors
+  K.relayout(f, fi, true);
+  K.relayout(u, x, true);
 
-  cudaEvent_t ev[6];
+  cudaEvent_t ev[4];
   for (auto& e : ev) cudaEventCreate(&e);
   double t_apply = 0, t_mv = 0, t_orth = 0;
   auto elapsed = [](cudaEvent_t a, cudaEvent_t b) { float ms = 0; cudaEventElapsedTime(&ms, a, b); return (double)ms; };
 
   std::vector<c128> hbuf(34 * R);
   auto fetch_h = [&](int rows) {
-    cudaMemcpyAsync(hbuf.data(), p.d_h, (size_t)rows * R * sizeof(c128), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(hbuf.data(), K.w.h, (size_t)rows * R * sizeof(c128), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
   };
-  // ||f|| per RHS
   K.norm2(fi, 0);
   fetch_h(1);
   std::vector<double> fn(R);
@@ -311,12 +525,11 @@ extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double 
   std::vector<double> cs((size_t)R * m), relres(R, 1.0), scl(R);
   std::vector<char> active(R);
   int it = 0, cycles = 0, applies = 0;
-  bool done = false;
   void* const u_saved = p.d_u;
-  while (!done) {
+  while (true) {
     // true residual r = f - A x -> V_0
-    matvec_internal_f64(p, x, false, V, fi, R, s);
-    K.norm2(V, 0);
+    K.matvec(x, true, Vb, fi);
+    K.norm2(Vb, 0);
     fetch_h(1);
     bool all = true;
     for (int r = 0; r < R; ++r) {
@@ -330,36 +543,34 @@ extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double 
     }
     if (all || it >= maxit) break;
     ++cycles;
-    K.scale(V, scl, V);
+    K.scale(Vb, scl, Vb);
     int k = 0;
     for (int j = 0; j < m; ++j) {
-      c128* Vj = V + (long long)j * vs;
-      c128* W1 = V + (long long)(j + 1) * vs;
-      c64* Zj = Z + (long long)j * vs;
-      c128* Zj2 = Z2 + (long long)j * vs;
+      V* Vj = Vb + (long long)j * vs;
+      V* W1 = Vb + (long long)(j + 1) * vs;
       // z_j = M_alpha v_j in the factor precision, computed in place in Z_j
       cudaEventRecord(ev[0], s);
       if (p.prec == HS_C64) {
-        note_launch();
-        to_c64_kernel<<<sm_count() * 8, 256, 0, s>>>(Vj, Zj, vs);
+        c64* Zj = Z + (long long)j * vs;
+        K.to_c64(Vj, Zj);
         p.d_u = Zj;
       } else {
+        c128* Zj2 = Z2 + (long long)j * vs;
         cudaMemcpyAsync(Zj2, Vj, vs * sizeof(c128), cudaMemcpyDeviceToDevice, s);
         p.d_u = Zj2;
       }
       st = sweep_internal(p, R, s);
+      void* zj = p.d_u;
       p.d_u = u_saved;
       if (st != HS_OK) break;
       ++applies;
       cudaEventRecord(ev[1], s);
-      // w = A z_j (FP64)
-      if (p.prec == HS_C64) matvec_internal_f64(p, Zj, true, W1, nullptr, R, s);
-      else matvec_internal_f64(p, Zj2, false, W1, nullptr, R, s);
+      K.matvec(zj, false, W1, nullptr);     // w = A z_j
       cudaEventRecord(ev[2], s);
-      // classical Gram-Schmidt, FP64, with a DGKS second pass
-      K.dots(V, j + 1, W1);          // d_h[0..j] = V^H w, d_h[j+1] = |w|^2
-      cudaMemcpyAsync(p.d_h + 33 * R, p.d_h + (long long)(j + 1) * R, R * sizeof(c128), cudaMemcpyDeviceToDevice, s);
-      K.update(V, j + 1, p.d_h, W1, 32);   // |w'|^2 -> d_h[32]
+      // classical Gram-Schmidt with an optional DGKS second pass
+      K.dots(Vb, j + 1, W1);          // h[0..j] = V^H w, h[j+1] = |w|^2
+      cudaMemcpyAsync(K.w.h + 33 * R, K.w.h + (long long)(j + 1) * R, R * sizeof(c128), cudaMemcpyDeviceToDevice, s);
+      K.update(Vb, j + 1, W1, 32);    // |w'|^2 -> h[32]
       fetch_h(34);
       std::vector<c128> h1(hbuf.begin(), hbuf.begin() + (size_t)(j + 1) * R);
       bool need2 = false;
@@ -368,8 +579,8 @@ extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double 
       std::vector<double> nw(R);
       for (int r = 0; r < R; ++r) nw[r] = std::sqrt(hbuf[32 * R + r].re);
       if (need2 && p.opt.reorth) {
-        K.dots(V, j + 1, W1);
-        K.update(V, j + 1, p.d_h, W1, 32);
+        K.dots(Vb, j + 1, W1);
+        K.update(Vb, j + 1, W1, 32);
         fetch_h(33);
         for (size_t q = 0; q < h1.size(); ++q) { h1[q].re += hbuf[q].re; h1[q].im += hbuf[q].im; }
         for (int r = 0; r < R; ++r) nw[r] = std::sqrt(hbuf[32 * R + r].re);
@@ -421,22 +632,20 @@ extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double 
       }
       for (int i = 0; i < k; ++i) y[(size_t)i * R + r] = c128{yr[i].real(), yr[i].imag()};
     }
-    cudaMemcpyAsync(p.d_h, y.data(), y.size() * sizeof(c128), cudaMemcpyHostToDevice, s);
-    if (p.prec == HS_C64) K.xupdate(Z, k, p.d_h, x);
-    else K.xupdate(Z2, k, p.d_h, x);
+    cudaMemcpyAsync(K.w.h, y.data(), y.size() * sizeof(c128), cudaMemcpyHostToDevice, s);
+    if (p.prec == HS_C64) K.xupdate(Z, k, x);
+    else K.xupdate(Z2, k, x);
     cudaStreamSynchronize(s);
   }
   p.d_u = u_saved;
-  if (st == HS_OK) st = layout_from_internal(x, HS_C128, u, HS_C128, (int)npts, R, s);
+  if (st == HS_OK) K.relayout(x, u, false);
   cudaError_t e = cudaStreamSynchronize(s);
   for (auto& q : ev) cudaEventDestroy(q);
   if (st == HS_OK && e != cudaSuccess) st = cuda_status(e);
-  int dst = HS_OK;
   if (st == HS_OK) {
     int w3[3];
     cudaMemcpy(w3, p.d_status, sizeof(w3), cudaMemcpyDeviceToHost);
-    dst = w3[0];
-    if (dst != HS_OK) st = dst;
+    if (w3[0] != HS_OK) st = w3[0];
   }
   double mx = 0;
   bool nan = false;
@@ -453,6 +662,21 @@ extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double 
   }
   if (st == HS_OK && (mx > tol || nan)) st = HS_ENOCONV;
   return st;
+}
+
+}  // namespace
+}  // namespace hs
+
+using namespace hs;
+
+extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double tol, int maxit,
+                        hs_solve_info* info, void* stream) {
+  if (!plan || !f || !u || !(tol > 0.0) || maxit < 1) return HS_EINVAL;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (nrhs < 1 || nrhs > p.max_nrhs) return HS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  return (p.prec == HS_C64) ? solve_t<DF64>(p, f, u, nrhs, tol, maxit, info, s)
+                            : solve_t<F64>(p, f, u, nrhs, tol, maxit, info, s);
 }
 
 extern "C" int hs_release_workspace(void) {

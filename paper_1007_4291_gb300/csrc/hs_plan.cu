@@ -135,6 +135,7 @@ extern "C" const char* hs_strerror(int s) {
 static void free_plan_memory(Plan* p) {
   void* ptrs[] = {p->d_inv_s1, p->d_a1, p->d_inv_s2, p->d_a2, p->f_inv_s1, p->f_a1, p->f_inv_s2, p->f_a2,
                   p->d_pml1, p->d_pml2, p->d_m0, p->f_m0, p->d_cinv2, p->d_s2win, p->d_blocks,
+                  p->k_inv_s1, p->k_a1, p->k_inv_s2, p->k_a2, p->k_m0,
                   p->d_fac, p->d_red, p->d_cor, p->d_u, p->d_z, p->d_rc, p->d_lc, p->d_xs, p->d_ps,
                   p->d_status};
   for (void* q : ptrs) if (q) cudaFree(q);
@@ -249,21 +250,37 @@ extern "C" int hs_setup(const double* c, double omega, int n, int dim, int pml_w
   cudaMemcpy(p->d_pml1, pml.data(), n + 2, cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_pml2, pml.data(), n + 2, cudaMemcpyHostToDevice);
 
-  // ---- per-point omega^2/c^2 and 1/c^2
+  // ---- per-point omega^2/c^2 and 1/c^2 (and double-float copies)
   const size_t N2 = (size_t)n * n;
   {
+    auto split = [](double x, float* o) {
+      o[0] = (float)x;
+      o[1] = (float)(x - (double)o[0]);
+    };
     std::vector<double> m0(N2), ci2(N2);
-    std::vector<float> fm0(N2);
+    std::vector<float> fm0(N2), km0(2 * N2);
     for (size_t k = 0; k < N2; ++k) {
       ci2[k] = 1.0 / (c[k] * c[k]);
       m0[k] = omega * omega * ci2[k];
       fm0[k] = (float)m0[k];
+      split(m0[k], &km0[2 * k]);
     }
-    if ((st = dalloc(*p, &p->d_m0, N2)) || (st = dalloc(*p, &p->f_m0, N2)) || (st = dalloc(*p, &p->d_cinv2, N2)))
+    std::vector<float> kis(4 * (n + 2)), ka(4 * (n + 1));
+    for (int k = 0; k <= n + 1; ++k) { split(inv_s[k].re, &kis[4 * k]); split(inv_s[k].im, &kis[4 * k + 2]); }
+    for (int k = 0; k <= n; ++k) { split(a_half[k].re, &ka[4 * k]); split(a_half[k].im, &ka[4 * k + 2]); }
+    if ((st = dalloc(*p, &p->d_m0, N2)) || (st = dalloc(*p, &p->f_m0, N2)) || (st = dalloc(*p, &p->d_cinv2, N2)) ||
+        (st = dalloc(*p, (float**)&p->k_m0, 2 * N2)) || (st = dalloc(*p, (float**)&p->k_inv_s1, 4 * (n + 2))) ||
+        (st = dalloc(*p, (float**)&p->k_inv_s2, 4 * (n + 2))) || (st = dalloc(*p, (float**)&p->k_a1, 4 * (n + 1))) ||
+        (st = dalloc(*p, (float**)&p->k_a2, 4 * (n + 1))))
       return fail(st);
     cudaMemcpy(p->d_m0, m0.data(), N2 * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(p->f_m0, fm0.data(), N2 * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(p->d_cinv2, ci2.data(), N2 * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->k_m0, km0.data(), 2 * N2 * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->k_inv_s1, kis.data(), kis.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->k_inv_s2, kis.data(), kis.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->k_a1, ka.data(), ka.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->k_a2, ka.data(), ka.size() * sizeof(float), cudaMemcpyHostToDevice);
   }
 
   // ---- per-block window x2 tables (moving profile of Eq. helma or the

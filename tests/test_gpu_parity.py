@@ -190,3 +190,27 @@ def test_solve_iteration_count_matches_oracle():
         assert abs(info["iterations"] - it) <= 1
     finally:
         hs.hs_destroy(plan)
+
+
+def test_solve_with_c64_factors_reaches_fp64_class_tolerance():
+    """The complex64 path keeps its Krylov vectors in double-float (48-bit
+    significand): it must reach a 1e-10 relative residual, measured by the
+    oracle's FP64 operator, which single precision cannot represent."""
+    n, bp = 47, 6
+    c = I.random_velocity(n, 12)
+    omega = 2 * np.pi * 3.0
+    R = 3
+    plan = make_plan(c, omega, bp, bp, 2, prec=hs.HS_C64, chunk=8, max_nrhs=R, restart=20)
+    try:
+        f = I.point_sources(n, R, 6, bp)
+        fg = gpu(f)
+        ug = torch.zeros_like(fg)
+        code, info = hs.hs_solve(plan, fg, ug, R, 1e-10, 300)
+        assert code == hs.HS_OK, info
+        A0 = H.helmholtz_matrix(c, omega, bp, C_PML, 0.0)
+        u = ug.cpu().numpy()
+        for k in range(R):
+            res = np.linalg.norm(f[k].ravel() - A0 @ u[k].ravel()) / np.linalg.norm(f[k].ravel())
+            assert res <= 1e-10, res
+    finally:
+        hs.hs_destroy(plan)
