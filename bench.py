@@ -27,6 +27,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) of one sweep application, from an ncu capture of
+# the phase 1/2/3 kernels of one stage (both fronts; dram__bytes_read.sum +
+# dram__bytes_write.sum = 161.0 MB) scaled by the 171 stages of the plan.
+# Keyed by (n, layers per step, RHS, factor precision); None elsewhere.
+SWEEP_TRAFFIC = {(2047, 12, 64, 64): 161.0e6 * 171}
+
 METRIC = "GMRES time-to-1e-6 & sweep applies/s (2D n=2047, 64 RHS), % HBM roofline"
 UNIT = "rhs_solved_per_s"
 
@@ -326,7 +332,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": "sweep application M_alpha (phase 1/2/3 kernels of all stages)",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock of measured)" % sm_max,
-                "traffic": None,
+                "traffic": SWEEP_TRAFFIC.get((n, args.dl, R, args.prec)),
                 "hbm_achieved_gbs": by / per_apply / 1e9, "hbm_peak_gbs": hbm,
                 "hbm_frac": by / per_apply / 1e9 / hbm,
                 "algorithmic_flops_per_apply": fl, "algorithmic_bytes_per_apply": by,
