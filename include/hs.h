@@ -57,6 +57,11 @@ typedef struct {
   int restart;           /* FGMRES restart length m.                                                  default 20 */
   int reorth;            /* 0: classical Gram-Schmidt; 1: CGS with a second pass when needed (DGKS).  default 0 */
   long long spin_budget; /* SM clock cycles a device-side barrier wait may take before HS_ETIMEOUT.   default 1<<30 */
+  int graphs;            /* 1: hs_apply and hs_solve replay the stage chain of the sweep as a CUDA
+                            graph (captured on first use per nrhs); 0: direct launches.          default 1 */
+  const char* tune_cache;/* path of the chunk-length table written by hs_autotune; with chunk = 0,
+                            hs_setup takes the chunk length from it when it holds the problem's
+                            key.  NULL: not used.  The string must outlive the hs_setup call.    default NULL */
 } hs_options;
 
 typedef struct hs_plan hs_plan;
@@ -99,6 +104,20 @@ int hs_setup(const double* c, double omega, int n, int dim, int pml_width, int m
              const hs_options* opt, void* stream, hs_plan** out);
 
 /*
+ * hs_setup_batched -- hs_setup for nprob independent problems of any sizes
+ * n[k] (Algorithm 3 for each; the subproblems of all of them are independent,
+ * Sec. 2.3) with shared widths and options.  c[k] is a HOST pointer to the
+ * n[k]*n[k] velocities of problem k and omega[k] its frequency.  All chunk
+ * factorisations of all problems run in one persistent launch, and all
+ * separator systems in a second one.  On success plans[k] receives problem
+ * k's plan (each later used and destroyed on its own); on any error no plan
+ * is returned and nothing stays allocated.
+ */
+int hs_setup_batched(int nprob, const double* const* c, const double* omega, const int* n, int dim,
+                     int pml_width, int moving_pml_width, const hs_options* opt, void* stream,
+                     hs_plan** plans);
+
+/*
  * hs_apply -- z = M_alpha r (Algorithm 4 with two fronts, Sec. 2.3).
  * r, z     device vectors of nrhs RHS (layout above), dtype HS_C64 or HS_C128;
  *          r and z may alias.  1 <= nrhs <= opt.max_nrhs.
@@ -130,6 +149,32 @@ int hs_apply(hs_plan* plan, const void* r, void* z, int nrhs, int dtype, void* s
  * Arguments as hs_apply.
  */
 int hs_apply_noalloc(hs_plan* plan, const void* r, void* z, int nrhs, int dtype, void* stream);
+
+/*
+ * hs_apply_batched -- z[k] = M_alpha^(k) r[k] for nprob distinct plans, as
+ * one CUDA graph whose per-problem stage chains run concurrently (small
+ * problems alone cannot fill the GPU).  The graph is captured on the first
+ * call for a given list of (plan, r, z, nrhs) and dtype and replayed after;
+ * destroying any of the plans drops it.  r[k], z[k]: device vectors of
+ * nrhs[k] RHS of plan k (1 <= nrhs[k] <= its max_nrhs), may alias.  A plan
+ * may appear once only (HS_EINVAL otherwise).
+ */
+int hs_apply_batched(int nprob, hs_plan* const* plans, const void* const* r, void* const* z, const int* nrhs,
+                     int dtype, void* stream);
+
+/*
+ * hs_autotune -- pick the x1 chunk length of the subproblem solves (the
+ * chunk count sets the CTAs per front of every sweep stage) for one problem
+ * shape by timing: for each candidate length it sets up the problem and times
+ * hs_apply of nrhs RHS with CUDA events on `stream`.  Writes the fastest
+ * length to *best_chunk (and its time per application in ms to *best_ms when
+ * not NULL).  When opt->tune_cache is set, appends the result to that text
+ * file under the key (n, pml_width, moving_pml_width, layers_per_step,
+ * factor_prec, nrhs), which later hs_setup calls with chunk = 0 and
+ * max_nrhs = nrhs read.  c is a HOST pointer as in hs_setup.
+ */
+int hs_autotune(const double* c, double omega, int n, int dim, int pml_width, int moving_pml_width,
+                const hs_options* opt, int nrhs, void* stream, int* best_chunk, double* best_ms);
 
 /*
  * hs_matvec -- y = A x with the Eq. helmd operator (alpha = 0).

@@ -19,7 +19,9 @@
 // pivoting inside the block (the block recursion itself is pivot-free);
 // a zero pivot sets HS_EBREAKDOWN in the plan's status word.
 //
-// One warp owns one (block, chunk) work item; lanes own matrix rows and all
+// One warp owns one (problem, block, chunk) work item and a single persistent
+// launch covers the items of every problem of a batch (any n, any window
+// height); lanes own matrix rows and all
 // work matrices live in shared memory (row stride W+1 complex, conflict-free).
 #include <algorithm>
 #include "hs_internal.cuh"
@@ -29,8 +31,7 @@ namespace hs {
 namespace {
 
 struct FactorArgs {
-  int n, L, P, nitems, nblocks;
-  const int* block_ids;
+  int n, L, P;
   const BlockDesc* blocks;
   const c128* inv_s1;
   const c128* a1;
@@ -172,8 +173,9 @@ __device__ __forceinline__ void store_rows(cplx<R>* dst, const cplx<R>* src, int
   }
 }
 
+// Factor chunk k of block bi: interior G_j, spikes, corner blocks.
 template <typename R, int W>
-__global__ void __launch_bounds__(32) factor_chunks_kernel(FactorArgs a) {
+__device__ __forceinline__ void chunk_item(const FactorArgs& a, const int bi, const int k) {
   using C = cplx<R>;
   constexpr int LD = W + 1;          // shared work matrices
   constexpr int LDP = W + 2;         // global payload rows (payload_ld)
@@ -189,9 +191,7 @@ __global__ void __launch_bounds__(32) factor_chunks_kernel(FactorArgs a) {
   C* facb = reinterpret_cast<C*>(a.fac);
   C* corb = reinterpret_cast<C*>(a.cor);
 
-  for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-    const int bi = a.block_ids[item / a.P];
-    const int k = (int)(item % a.P);
+  {
     const BlockDesc d = a.blocks[bi];
     const long long pe = payload_elems(W, d.d_out);
     C* fac = facb + d.fac_off;
@@ -280,8 +280,9 @@ __global__ void __launch_bounds__(32) factor_chunks_kernel(FactorArgs a) {
 //   Sigma_kk   = D_s - C_{s-1} G^{(k)}_r C_{s-1} - C_s W^{(k+1)}_l C_s
 //   Sigma_k,k-1 = -C_{s-1} W^{(k)}_r C_{s'}        (s' = previous separator)
 //   F_k = Sigma_k,k-1 Gamma_{k-1},  Gamma_k = (Sigma_kk - F_k Sigma_k,k-1^t)^{-1}
+// Reduced (separator) system of block bi.
 template <typename R, int W>
-__global__ void __launch_bounds__(32) factor_reduced_kernel(FactorArgs a) {
+__device__ __forceinline__ void reduced_item(const FactorArgs& a, const int bi) {
   using C = cplx<R>;
   constexpr int LD = W + 1;          // shared work matrices and corner blocks
   constexpr int LDP = W + 2;         // global payload rows (payload_ld)
@@ -297,8 +298,7 @@ __global__ void __launch_bounds__(32) factor_reduced_kernel(FactorArgs a) {
   C* facb = reinterpret_cast<C*>(a.fac);
   C* corb = reinterpret_cast<C*>(a.cor);
   C* redb = reinterpret_cast<C*>(a.red);
-  for (int item = blockIdx.x; item < a.nblocks; item += gridDim.x) {
-    const int bi = a.block_ids[item];
+  {
     const BlockDesc d = a.blocks[bi];
     (void)facb;
     for (int t = lane; t < 3 * d.w; t += 32) s2[t] = a.s2win[d.s2_off + t];
@@ -372,63 +372,119 @@ __global__ void __launch_bounds__(32) factor_reduced_kernel(FactorArgs a) {
   }
 }
 
-template <typename R, int W>
-int launch_w(Plan& p, FactorArgs a, const std::vector<int>& ids, cudaStream_t s) {
-  if (ids.empty()) return HS_OK;
-  int* d_ids = nullptr;
-  HS_CUDA_TRY(cudaMalloc(&d_ids, ids.size() * sizeof(int)));
-  cudaMemcpyAsync(d_ids, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice, s);
-  a.block_ids = d_ids;
-  a.nblocks = (int)ids.size();
-  a.nitems = (int)ids.size() * p.P;
-  const size_t smem = 4 * sizeof(cplx<R>) * W * (W + 1) + 2 * sizeof(cplx<R>) * W + 3 * 32 * sizeof(c128) +
-                      32 * sizeof(int);
-  cudaFuncSetAttribute(factor_chunks_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(factor_reduced_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // One persistent launch over all (block, chunk) work items of this width.
-  int grid = std::min<long long>(a.nitems, (long long)sms * 16);
-  note_launch();
-  factor_chunks_kernel<R, W><<<grid, 32, smem, s>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess && p.P > 1) {
-    int g2 = std::min(a.nblocks, sms * 16);
-    note_launch();
-    factor_reduced_kernel<R, W><<<g2, 32, smem, s>>>(a);
-    e = cudaGetLastError();
+// One work item of the batched setup: a chunk of a block of a problem.
+struct FactorItem {
+  int prob, block, chunk, W;
+};
+
+// Persistent launches over the work items of all problems of a batch; the
+// window height W (uniform per item) selects the instantiation.
+template <typename R>
+__global__ void __launch_bounds__(32) factor_chunks_kernel(const FactorArgs* probs, const FactorItem* items, int nitems) {
+  for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+    const FactorItem it = items[i];
+    const FactorArgs a = probs[it.prob];
+    switch (it.W) {
+      case 8: chunk_item<R, 8>(a, it.block, it.chunk); break;
+      case 12: chunk_item<R, 12>(a, it.block, it.chunk); break;
+      case 16: chunk_item<R, 16>(a, it.block, it.chunk); break;
+      case 24: chunk_item<R, 24>(a, it.block, it.chunk); break;
+      case 32: chunk_item<R, 32>(a, it.block, it.chunk); break;
+      default: if (threadIdx.x == 0) set_status(a.status, HS_EUNSUPPORTED, it.block, it.chunk);
+    }
+    __syncwarp();
   }
-  cudaStreamSynchronize(s);
-  cudaFree(d_ids);
-  if (e != cudaSuccess) return cuda_status(e);
-  return HS_OK;
 }
 
 template <typename R>
-int launch_setup_t(Plan& p, cudaStream_t s) {
-  FactorArgs a{};
-  a.n = p.n; a.L = p.L; a.P = p.P;
-  a.blocks = p.d_blocks;
-  a.inv_s1 = p.d_inv_s1; a.a1 = p.d_a1; a.cinv2 = p.d_cinv2; a.s2win = p.d_s2win;
-  const double wr = p.omega, wi = p.alpha;
-  a.wst2 = c128{wr * wr - wi * wi, 2 * wr * wi};
-  a.fac = p.d_fac; a.red = p.d_red; a.cor = p.d_cor; a.status = p.d_status;
-  std::vector<int> by_w[33];
-  for (int i = 0; i < (int)p.blocks.size(); ++i) by_w[p.blocks[i].W].push_back(i);
-  int st = HS_OK;
-  if (st == HS_OK) st = launch_w<R, 8>(p, a, by_w[8], s);
-  if (st == HS_OK) st = launch_w<R, 12>(p, a, by_w[12], s);
-  if (st == HS_OK) st = launch_w<R, 16>(p, a, by_w[16], s);
-  if (st == HS_OK) st = launch_w<R, 24>(p, a, by_w[24], s);
-  if (st == HS_OK) st = launch_w<R, 32>(p, a, by_w[32], s);
-  return st;
+__global__ void __launch_bounds__(32) factor_reduced_kernel(const FactorArgs* probs, const FactorItem* items, int nitems) {
+  for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+    const FactorItem it = items[i];
+    const FactorArgs a = probs[it.prob];
+    switch (it.W) {
+      case 8: reduced_item<R, 8>(a, it.block); break;
+      case 12: reduced_item<R, 12>(a, it.block); break;
+      case 16: reduced_item<R, 16>(a, it.block); break;
+      case 24: reduced_item<R, 24>(a, it.block); break;
+      case 32: reduced_item<R, 32>(a, it.block); break;
+      default: if (threadIdx.x == 0) set_status(a.status, HS_EUNSUPPORTED, it.block, -1);
+    }
+    __syncwarp();
+  }
+}
+
+template <typename R>
+size_t factor_smem(int W) {
+  return 4 * sizeof(cplx<R>) * W * (W + 1) + 2 * sizeof(cplx<R>) * W + 3 * 32 * sizeof(c128) + 32 * sizeof(int);
+}
+
+template <typename R>
+int launch_setup_t(const std::vector<Plan*>& ps, cudaStream_t s) {
+  std::vector<FactorArgs> args;
+  std::vector<FactorItem> items, reduced;
+  int Wmax = 8;
+  for (int q = 0; q < (int)ps.size(); ++q) {
+    const Plan& p = *ps[q];
+    FactorArgs a{};
+    a.n = p.n; a.L = p.L; a.P = p.P;
+    a.blocks = p.d_blocks;
+    a.inv_s1 = p.d_inv_s1; a.a1 = p.d_a1; a.cinv2 = p.d_cinv2; a.s2win = p.d_s2win;
+    const double wr = p.omega, wi = p.alpha;
+    a.wst2 = c128{wr * wr - wi * wi, 2 * wr * wi};
+    a.fac = p.d_fac; a.red = p.d_red; a.cor = p.d_cor; a.status = p.d_status;
+    args.push_back(a);
+    for (int b = 0; b < (int)p.blocks.size(); ++b) {
+      const int W = p.blocks[b].W;
+      Wmax = std::max(Wmax, W);
+      for (int k = 0; k < p.P; ++k) items.push_back({q, b, k, W});
+      if (p.P > 1) reduced.push_back({q, b, 0, W});
+    }
+  }
+  // longest items first: windows of height W cost ~W^3 per column
+  auto wider = [](const FactorItem& x, const FactorItem& y) { return x.W > y.W; };
+  std::stable_sort(items.begin(), items.end(), wider);
+  std::stable_sort(reduced.begin(), reduced.end(), wider);
+  const size_t abytes = ((args.size() * sizeof(FactorArgs) + 255) / 256) * 256;
+  const size_t ibytes = items.size() * sizeof(FactorItem), rbytes = reduced.size() * sizeof(FactorItem);
+  char* buf = nullptr;
+  HS_CUDA_TRY(cudaMalloc(&buf, abytes + ibytes + rbytes + 16));
+  FactorArgs* d_args = reinterpret_cast<FactorArgs*>(buf);
+  FactorItem* d_items = reinterpret_cast<FactorItem*>(buf + abytes);
+  FactorItem* d_red = reinterpret_cast<FactorItem*>(buf + abytes + ibytes);
+  cudaMemcpyAsync(d_args, args.data(), args.size() * sizeof(FactorArgs), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(d_items, items.data(), ibytes, cudaMemcpyHostToDevice, s);
+  if (rbytes) cudaMemcpyAsync(d_red, reduced.data(), rbytes, cudaMemcpyHostToDevice, s);
+  const size_t smem = factor_smem<R>(Wmax);
+  cudaFuncSetAttribute(factor_chunks_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(factor_reduced_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaSuccess;
+  if (!items.empty()) {
+    const int grid = (int)std::min<long long>((long long)items.size(), (long long)sms * 16);
+    note_launch();
+    factor_chunks_kernel<R><<<grid, 32, smem, s>>>(d_args, d_items, (int)items.size());
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && !reduced.empty()) {
+    const int g2 = (int)std::min<long long>((long long)reduced.size(), (long long)sms * 16);
+    note_launch();
+    factor_reduced_kernel<R><<<g2, 32, smem, s>>>(d_args, d_red, (int)reduced.size());
+    e = cudaGetLastError();
+  }
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (e2 != cudaSuccess) return cuda_status(e2);
+  return HS_OK;
 }
 
 }  // namespace
 
-int launch_setup(Plan& p, cudaStream_t s) {
-  return (p.prec == HS_C64) ? launch_setup_t<float>(p, s) : launch_setup_t<double>(p, s);
+int launch_setup(const std::vector<Plan*>& ps, cudaStream_t s) {
+  if (ps.empty()) return HS_OK;
+  return (ps[0]->prec == HS_C64) ? launch_setup_t<float>(ps, s) : launch_setup_t<double>(ps, s);
 }
 
 }  // namespace hs

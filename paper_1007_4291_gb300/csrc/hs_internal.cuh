@@ -6,6 +6,7 @@
 #include <vector>
 #include <string>
 #include <atomic>
+#include <mutex>
 #include "hs.h"
 
 namespace hs {
@@ -105,6 +106,8 @@ struct Plan {
   void* d_ps = nullptr;     // separator forward values psi
   int* d_status = nullptr;  // device status word(s): [0] code, [1] block, [2] column
   long long bytes = 0;
+  long long uid = 0;        // process-unique id (keys of cached CUDA graphs)
+  void* graphs = nullptr;   // cached executable graphs of this plan's sweep (hs_sweep.cu)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -116,9 +119,47 @@ inline void note_launch(long long k = 1) { g_launches.fetch_add(k, std::memory_o
 
 int padded_width(int w);   // 8, 12, 16, 24, 32 or -1
 
+// Capture the launches body(stream) makes on `cap` into an executable graph.
+// Kernels counted by note_launch during the capture did not run: they are
+// taken back and returned in *kernels, to be counted at each replay.
+template <typename F>
+int capture_graph(cudaStream_t cap, F&& body, cudaGraphExec_t* exec, long long* kernels) {
+  const long long before = g_launches.load();
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int st = body(cap);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(cap, &g);
+  const long long k = g_launches.load() - before;
+  g_launches.fetch_sub(k);
+  if (st != HS_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st != HS_OK ? st : cuda_status(e);
+  }
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_status(e);
+  *kernels = k;
+  return HS_OK;
+}
+
 // launchers (defined in the .cu files)
-int launch_setup(Plan& p, cudaStream_t s);
-int sweep_internal(Plan& p, int nrhs, cudaStream_t s);           // u <- M_alpha u on p.d_u
+// factor every block of every plan of `ps` (same factor precision): one
+// launch over all chunks, one over all reduced systems; synchronises `s`
+int launch_setup(const std::vector<Plan*>& ps, cudaStream_t s);
+// u <- M_alpha u on p.d_u.  graph: replay (or capture on first use) the
+// stage chain as one CUDA graph keyed by nrhs and the scratch pointers.
+int sweep_internal(Plan& p, int nrhs, cudaStream_t s, bool graph = false);
+// direct launches of the stage chain (used inside captures)
+int sweep_launch(Plan& p, int nrhs, cudaStream_t s);
+void release_sweep_graphs(Plan& p);
+// chunk length stored by hs_autotune in `path` for this key (0 if none)
+int tuned_chunk(const char* path, int n, int bp, int b, int dL, int prec, int nrhs);
+// drop cached multi-plan graphs that contain plan `uid` (hs_batch.cu)
+void forget_batch_graphs(long long uid);
+// set the shared-memory attributes of every sweep kernel (before a capture)
+void sweep_prepare_attributes(int prec);
 int layout_to_internal(const void* src, int dtype, void* dst, int prec, int n2, int R, cudaStream_t s);
 int layout_from_internal(const void* src, int prec, void* dst, int dtype, int n2, int R, cudaStream_t s);
 int matvec_abi(Plan& p, const void* x, void* y, int nrhs, int dtype, cudaStream_t s);

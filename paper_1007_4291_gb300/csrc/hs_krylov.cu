@@ -559,7 +559,7 @@ int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs
         cudaMemcpyAsync(Zj2, Vj, vs * sizeof(c128), cudaMemcpyDeviceToDevice, s);
         p.d_u = Zj2;
       }
-      st = sweep_internal(p, R, s);
+      st = sweep_internal(p, R, s, p.opt.graphs != 0);
       void* zj = p.d_u;
       p.d_u = u_saved;
       if (st != HS_OK) break;

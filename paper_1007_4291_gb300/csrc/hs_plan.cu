@@ -115,6 +115,8 @@ extern "C" int hs_default_options(hs_options* opt) {
   opt->restart = 20;
   opt->reorth = 0;
   opt->spin_budget = 1LL << 30;
+  opt->graphs = 1;
+  opt->tune_cache = nullptr;
   return HS_OK;
 }
 
@@ -145,6 +147,8 @@ extern "C" int hs_destroy(hs_plan* plan) {
   if (!plan) return HS_OK;
   Plan* p = reinterpret_cast<Plan*>(plan);
   cudaDeviceSynchronize();
+  forget_batch_graphs(p->uid);
+  release_sweep_graphs(*p);
   free_plan_memory(p);
   delete p;
   return HS_OK;
@@ -175,9 +179,11 @@ extern "C" int hs_sync(hs_plan* plan, void* stream) {
   return hs_last_device_status(plan);
 }
 
-extern "C" int hs_setup(const double* c, double omega, int n, int dim, int pml_width, int moving_pml_width,
-                        const hs_options* opt_in, void* stream, hs_plan** out) {
-  if (!out) return HS_EINVAL;
+// Validate the arguments, build the host tables of one problem and allocate
+// and fill its device memory (no kernel launches).  On failure nothing is
+// left allocated.
+static int prepare_plan(const double* c, double omega, int n, int dim, int pml_width, int moving_pml_width,
+                        const hs_options* opt_in, Plan** out) {
   *out = nullptr;
   if (!c || !(omega > 0.0) || !std::isfinite(omega)) return HS_EINVAL;
   if (dim != 2) return (dim == 3) ? HS_EUNSUPPORTED : HS_EINVAL;
@@ -206,7 +212,11 @@ extern "C" int hs_setup(const double* c, double omega, int n, int dim, int pml_w
   // x1 chunking of the subproblem solves (>= 2 columns per chunk).
   // (at most 64 separators: the separator solve keeps their right-hand
   // sides in shared memory)
-  p->L = opt.chunk ? opt.chunk : 32;
+  int chunk = opt.chunk;
+  if (chunk == 0) chunk = tuned_chunk(opt.tune_cache, n, pml_width, moving_pml_width, opt.layers_per_step,
+                                      opt.factor_prec, opt.max_nrhs);
+  p->opt.tune_cache = nullptr;  // the string belongs to the caller
+  p->L = chunk ? chunk : 32;
   p->L = std::max(p->L, (n + 64) / 65);
   if (p->L > n) p->L = n;
   if (p->L < 2) p->L = 2;
@@ -327,15 +337,62 @@ extern "C" int hs_setup(const double* c, double omega, int n, int dim, int pml_w
       return fail(st);
   }
   if (cudaGetLastError() != cudaSuccess) return fail(HS_ECUDA);
+  static std::atomic<long long> next_uid{1};
+  p->uid = next_uid.fetch_add(1);
+  *out = p;
+  return HS_OK;
+}
 
-  cudaStream_t s = (cudaStream_t)stream;
-  st = launch_setup(*p, s);
-  if (st != HS_OK) return fail(st);
-  cudaError_t e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail(cuda_status(e));
-  int dst[3];
-  cudaMemcpy(dst, p->d_status, sizeof(dst), cudaMemcpyDeviceToHost);
-  if (dst[0] != HS_OK) return fail(dst[0]);
+static void drop_plan(Plan* p) {
+  release_sweep_graphs(*p);
+  free_plan_memory(p);
+  delete p;
+}
+
+// Factor the prepared plans together and check their status words.
+static int factor_plans(std::vector<Plan*>& ps, cudaStream_t s) {
+  int st = launch_setup(ps, s);
+  if (st != HS_OK) return st;
+  for (Plan* p : ps) {
+    int dst[3];
+    if (cudaMemcpy(dst, p->d_status, sizeof(dst), cudaMemcpyDeviceToHost) != cudaSuccess) return HS_ECUDA;
+    if (dst[0] != HS_OK) return dst[0];
+  }
+  return HS_OK;
+}
+
+extern "C" int hs_setup(const double* c, double omega, int n, int dim, int pml_width, int moving_pml_width,
+                        const hs_options* opt, void* stream, hs_plan** out) {
+  if (!out) return HS_EINVAL;
+  *out = nullptr;
+  Plan* p = nullptr;
+  int st = prepare_plan(c, omega, n, dim, pml_width, moving_pml_width, opt, &p);
+  if (st != HS_OK) return st;
+  std::vector<Plan*> ps{p};
+  st = factor_plans(ps, (cudaStream_t)stream);
+  if (st != HS_OK) { drop_plan(p); return st; }
   *out = reinterpret_cast<hs_plan*>(p);
+  return HS_OK;
+}
+
+extern "C" int hs_setup_batched(int nprob, const double* const* c, const double* omega, const int* n, int dim,
+                                int pml_width, int moving_pml_width, const hs_options* opt, void* stream,
+                                hs_plan** out) {
+  if (nprob < 1 || !c || !omega || !n || !out) return HS_EINVAL;
+  for (int k = 0; k < nprob; ++k) out[k] = nullptr;
+  if (opt && opt->factor_prec != HS_C64 && opt->factor_prec != HS_C128) return HS_EINVAL;
+  std::vector<Plan*> ps;
+  int st = HS_OK;
+  for (int k = 0; k < nprob && st == HS_OK; ++k) {
+    Plan* p = nullptr;
+    st = prepare_plan(c[k], omega[k], n[k], dim, pml_width, moving_pml_width, opt, &p);
+    if (st == HS_OK) ps.push_back(p);
+  }
+  if (st == HS_OK) st = factor_plans(ps, (cudaStream_t)stream);
+  if (st != HS_OK) {
+    for (Plan* p : ps) drop_plan(p);
+    return st;
+  }
+  for (int k = 0; k < nprob; ++k) out[k] = reinterpret_cast<hs_plan*>(ps[k]);
   return HS_OK;
 }

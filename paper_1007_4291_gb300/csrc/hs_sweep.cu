@@ -159,7 +159,10 @@ __device__ __forceinline__ void ring_producer(uint64_t* full, uint64_t* empty, i
     }
     issue(t);
   }
-  for (int u = (t > S ? t - S : 0); u < t; ++u) (void)mbar_wait_bounded(&full[u % S], (u / S) & 1, spin);
+  // drain: copies already issued must land before the CTA may exit, so this
+  // wait does not shrink with a small `spin` (a copy lands in microseconds)
+  const long long drain = spin > (1LL << 27) ? spin : (1LL << 27);
+  for (int u = (t > S ? t - S : 0); u < t; ++u) (void)mbar_wait_bounded(&full[u % S], (u / S) & 1, drain);
 }
 
 // ---------------------------------------------------------------- phases 1 and 3
@@ -203,6 +206,23 @@ __device__ __forceinline__ void st2<float>(cplx<float>* p, cplx<float> a, cplx<f
 
 __device__ __forceinline__ void consumer_barrier(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Consumer barrier that also returns the AND of `v` over the consumer
+// threads: after a bounded wait every consumer learns whether all of them
+// got their data, so they continue or stop together (a thread that stopped
+// alone would leave the others blocked on the next barrier).
+__device__ __forceinline__ bool consumer_barrier_and(int nthreads, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(nthreads)
+      : "memory");
+  return r != 0;
 }
 
 // Shared-memory bytes of phases 1 and 3.
@@ -316,8 +336,8 @@ __global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase1_kernel(SweepA
     const C* cc = V + d.d_out * LDP;
     const C* Y = ybuf + (t & 1) * (W * LDR);
     const C* Gi = gbuf + (t & 1) * (W * LDR);
-    ok = mbar_wait_bounded(&full[t % S13], (t / S13) & 1, a.spin);
-    if (!ok) return;
+    const bool landed = mbar_wait_bounded(&full[t % S13], (t / S13) & 1, a.spin);
+    if (landed) {
 #pragma unroll
     for (int q = 0; q < RPT; ++q)
 #pragma unroll
@@ -376,8 +396,9 @@ __global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase1_kernel(SweepA
       put_tile(ybuf + ((t + 1) & 1) * (W * LDR), yn);
       put_tile(gbuf + ((t + 1) & 1) * (W * LDR), gn);
     }
-    consumer_barrier(NCONS);
-    if (tid == 0) mbar_arrive(&empty[t % S13]);
+    }  // landed
+    ok = consumer_barrier_and(NCONS, landed);
+    if (ok && tid == 0) mbar_arrive(&empty[t % S13]);
   };
   for (int t = 0; t < ncol; t += 2) {
     step(t, ra);
@@ -502,7 +523,7 @@ __global__ void __launch_bounds__(NT + 32) phase2_kernel(SweepArgs a) {
   int t = 0;
   for (int k = 0; k < nsep; ++k, ++t) {
     const C* F = stage(t) + W * LDP;
-    ok = mbar_wait_bounded(&full[t % S2], (t / S2) & 1, a.spin);
+    ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[t % S2], (t / S2) & 1, a.spin));
     if (!ok) break;
     C s0 = myrz[k * W + pl], s1{0, 0}, s2{0, 0}, s3{0, 0};
     if (k > 0) {
@@ -526,7 +547,7 @@ __global__ void __launch_bounds__(NT + 32) phase2_kernel(SweepArgs a) {
   for (int k = nsep - 1; k >= 0 && ok; --k, ++t) {
     const C* Gm = stage(t);
     const C* F = Gm + W * LDP;
-    ok = mbar_wait_bounded(&full[t % S2], (t / S2) & 1, a.spin);
+    ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[t % S2], (t / S2) & 1, a.spin));
     if (!ok) break;
     // Gamma_k psi_k: Gamma_k is symmetric, so lane p reads column p (no
     // bank conflicts); psi_k is read by every lane
@@ -664,15 +685,17 @@ __global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase3_kernel(SweepA
     const C* cc = V + d.d_out * LDP;
     const C* zt = ztile(t);
     C* TV = tvbuf + (t & 1) * (W * LDR);
-    ok = mbar_wait_bounded(&full[t % S13], (t / S13) & 1, a.spin);
-    if (!ok) return;
+    const bool landed = mbar_wait_bounded(&full[t % S13], (t / S13) & 1, a.spin);
     // tv = C_j x_{j+1} (own tile), shared through shared memory
+    if (landed) {
 #pragma unroll
-    for (int i = 0; i < ROWS; ++i) {
-      const C ci = cc[rg + NRG * i];
-      st2(TV + (rg + NRG * i) * LDR + c0, cmul(ci, x[0][i]), cmul(ci, x[1][i]));
+      for (int i = 0; i < ROWS; ++i) {
+        const C ci = cc[rg + NRG * i];
+        st2(TV + (rg + NRG * i) * LDR + c0, cmul(ci, x[0][i]), cmul(ci, x[1][i]));
+      }
     }
-    consumer_barrier(NCONS);
+    ok = consumer_barrier_and(NCONS, landed);
+    if (!ok) return;
     if (tid == 0 && t > 0) mbar_arrive(&empty[(t - 1) % S13]);   // every read of stage t-1 is done
 #pragma unroll
     for (int q = 0; q < RPT; ++q)
@@ -755,18 +778,27 @@ __global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase3_kernel(SweepA
 }
 
 template <typename R, int W>
+void set_attrs_w() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(phase1_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(phase3_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(phase2_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  });
+}
+
+template <typename R>
+void set_attrs() {
+  set_attrs_w<R, 8>(); set_attrs_w<R, 12>(); set_attrs_w<R, 16>(); set_attrs_w<R, 24>(); set_attrs_w<R, 32>();
+}
+
+template <typename R, int W>
 int run_stage_w(const Plan& p, SweepArgs a, cudaStream_t s) {
   using TL = Tile13<R, W>;
   const int dmax = std::max(a.blk[0].d_out, a.nfront > 1 ? a.blk[1].d_out : 0);
   const size_t sm1 = tile_smem<R, W>(dmax, false);
   const size_t sm3 = tile_smem<R, W>(dmax, true);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(phase1_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    cudaFuncSetAttribute(phase3_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    cudaFuncSetAttribute(phase2_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr_set = true;
-  }
+  set_attrs_w<R, W>();
   if (sm1 > 220 * 1024 || sm3 > 220 * 1024 || phase2_smem<R, W>(a.P - 1) > 220 * 1024) return HS_EUNSUPPORTED;
   dim3 g13(a.P, (a.R + TL::RG - 1) / TL::RG, a.nfront);
   note_launch();
@@ -873,8 +905,63 @@ int relayout(const void* src, void* dst, long long npts, int R, cudaStream_t s) 
 
 }  // namespace
 
-int sweep_internal(Plan& p, int nrhs, cudaStream_t s) {
+void sweep_prepare_attributes(int prec) {
+  if (prec == HS_C64) set_attrs<float>(); else set_attrs<double>();
+}
+
+int sweep_launch(Plan& p, int nrhs, cudaStream_t s) {
   return (p.prec == HS_C64) ? sweep_t<float>(p, nrhs, s) : sweep_t<double>(p, nrhs, s);
+}
+
+namespace {
+// Executable graphs of one plan's stage chain, keyed by the number of RHS and
+// the scratch buffers the kernels address.
+struct SweepGraphs {
+  struct Entry {
+    int nrhs;
+    void* ptrs[6];
+    cudaGraphExec_t exec;
+    long long kernels;
+  };
+  std::mutex m;
+  std::vector<Entry> list;
+  cudaStream_t cap = nullptr;
+};
+}  // namespace
+
+int sweep_internal(Plan& p, int nrhs, cudaStream_t s, bool graph) {
+  if (!graph) return sweep_launch(p, nrhs, s);
+  if (!p.graphs) p.graphs = new SweepGraphs();
+  SweepGraphs& gs = *static_cast<SweepGraphs*>(p.graphs);
+  std::lock_guard<std::mutex> lock(gs.m);
+  void* const ptrs[6] = {p.d_u, p.d_z, p.d_rc, p.d_lc, p.d_xs, p.d_ps};
+  for (auto& e : gs.list) {
+    if (e.nrhs == nrhs && std::equal(ptrs, ptrs + 6, e.ptrs)) {
+      note_launch(e.kernels);
+      cudaError_t ce = cudaGraphLaunch(e.exec, s);
+      return ce == cudaSuccess ? HS_OK : cuda_status(ce);
+    }
+  }
+  sweep_prepare_attributes(p.prec);
+  if (!gs.cap) HS_CUDA_TRY(cudaStreamCreateWithFlags(&gs.cap, cudaStreamNonBlocking));
+  SweepGraphs::Entry e{};
+  e.nrhs = nrhs;
+  std::copy(ptrs, ptrs + 6, e.ptrs);
+  int st = capture_graph(gs.cap, [&](cudaStream_t c) -> int { return sweep_launch(p, nrhs, c); }, &e.exec, &e.kernels);
+  if (st != HS_OK) return st;
+  gs.list.push_back(e);
+  note_launch(e.kernels);
+  cudaError_t ce = cudaGraphLaunch(e.exec, s);
+  return ce == cudaSuccess ? HS_OK : cuda_status(ce);
+}
+
+void release_sweep_graphs(Plan& p) {
+  if (!p.graphs) return;
+  SweepGraphs* gs = static_cast<SweepGraphs*>(p.graphs);
+  for (auto& e : gs->list) cudaGraphExecDestroy(e.exec);
+  if (gs->cap) cudaStreamDestroy(gs->cap);
+  delete gs;
+  p.graphs = nullptr;
 }
 
 int layout_to_internal(const void* src, int dtype, void* dst, int prec, int n2, int R, cudaStream_t s) {
@@ -902,7 +989,7 @@ extern "C" int hs_apply(hs_plan* plan, const void* r, void* z, int nrhs, int dty
   cudaStream_t s = (cudaStream_t)stream;
   const int n2 = p.n * p.n;
   int st = layout_to_internal(r, dtype, p.d_u, p.prec, n2, nrhs, s);
-  if (st == HS_OK) st = sweep_internal(p, nrhs, s);
+  if (st == HS_OK) st = sweep_internal(p, nrhs, s, p.opt.graphs != 0);
   if (st == HS_OK) st = layout_from_internal(p.d_u, p.prec, z, dtype, n2, nrhs, s);
   return st;
 }

@@ -18,14 +18,16 @@ LIBPATH = os.path.join(HERE, "libhs.so")
 HS_OK, HS_EINVAL, HS_ENOMEM, HS_EBREAKDOWN, HS_ETIMEOUT, HS_ENOCONV, HS_ECUDA, HS_EUNSUPPORTED = range(8)
 HS_C64, HS_C128 = 64, 128
 
-EXPORTED = ["hs_default_options", "hs_setup", "hs_apply", "hs_matvec", "hs_solve", "hs_sync",
-            "hs_last_device_status", "hs_plan_bytes", "hs_destroy", "hs_strerror"]
+EXPORTED = ["hs_default_options", "hs_setup", "hs_setup_batched", "hs_apply", "hs_apply_batched",
+            "hs_apply_noalloc", "hs_autotune", "hs_matvec", "hs_solve", "hs_sync", "hs_last_device_status",
+            "hs_plan_bytes", "hs_release_workspace", "hs_kernel_launches", "hs_destroy", "hs_strerror"]
 
 
 class HsOptions(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("pml_C", ctypes.c_double), ("layers_per_step", ctypes.c_int),
                 ("factor_prec", ctypes.c_int), ("chunk", ctypes.c_int), ("max_nrhs", ctypes.c_int),
-                ("restart", ctypes.c_int), ("reorth", ctypes.c_int), ("spin_budget", ctypes.c_longlong)]
+                ("restart", ctypes.c_int), ("reorth", ctypes.c_int), ("spin_budget", ctypes.c_longlong),
+                ("graphs", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
 
 
 class HsSolveInfo(ctypes.Structure):
@@ -56,6 +58,12 @@ def load(path=None):
     lib.hs_default_options.argtypes = [ctypes.POINTER(HsOptions)]
     lib.hs_setup.argtypes = [vp, d, i, i, i, i, ctypes.POINTER(HsOptions), vp, ctypes.POINTER(vp)]
     lib.hs_apply.argtypes = [vp, vp, vp, i, i, vp]
+    lib.hs_setup_batched.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(d), ctypes.POINTER(i), i, i, i,
+                                     ctypes.POINTER(HsOptions), vp, ctypes.POINTER(vp)]
+    lib.hs_apply_batched.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(i), i, vp]
+    lib.hs_autotune.argtypes = [vp, d, i, i, i, i, ctypes.POINTER(HsOptions), i, vp, ctypes.POINTER(i),
+                                ctypes.POINTER(d)]
     lib.hs_matvec.argtypes = [vp, vp, vp, i, i, vp]
     lib.hs_apply_noalloc.argtypes = [vp, vp, vp, i, i, vp]
     lib.hs_apply_noalloc.restype = i
@@ -67,8 +75,11 @@ def load(path=None):
     lib.hs_destroy.argtypes = [vp]
     lib.hs_strerror.argtypes = [i]
     lib.hs_strerror.restype = ctypes.c_char_p
+    lib.hs_release_workspace.argtypes = []
+    lib.hs_kernel_launches.argtypes = []
+    lib.hs_kernel_launches.restype = ll
     for name in EXPORTED:
-        if name not in ("hs_plan_bytes", "hs_strerror"):
+        if name not in ("hs_plan_bytes", "hs_strerror", "hs_kernel_launches"):
             getattr(lib, name).restype = i
     _LIB = lib
     return lib
@@ -113,6 +124,8 @@ def hs_default_options(**kw):
     for k, v in kw.items():
         if not hasattr(o, k):
             raise KeyError(k)
+        if k == "tune_cache" and isinstance(v, str):
+            v = v.encode()
         setattr(o, k, v)
     return o
 
@@ -128,6 +141,55 @@ def hs_setup(c, omega, n, dim, pml_width, moving_pml_width, opt=None, stream=Non
     _check(lib.hs_setup(c.ctypes.data, float(omega), int(n), int(dim), int(pml_width), int(moving_pml_width),
                         ctypes.byref(o), _stream(stream), ctypes.byref(plan)), "hs_setup")
     return plan
+
+
+def hs_setup_batched(cs, omegas, ns, dim, pml_width, moving_pml_width, opt=None, stream=None):
+    """Plans of several problems (host velocities cs[k] of ns[k]**dim points),
+    all factored in one launch.  Returns the list of plans."""
+    lib = load()
+    k = len(cs)
+    arrs = [np.ascontiguousarray(c, dtype=np.float64) for c in cs]
+    for a, n in zip(arrs, ns):
+        if a.size != n ** dim:
+            raise ValueError("c must hold n**dim values")
+    cp = (ctypes.c_void_p * k)(*[a.ctypes.data for a in arrs])
+    om = (ctypes.c_double * k)(*[float(w) for w in omegas])
+    nn = (ctypes.c_int * k)(*[int(n) for n in ns])
+    out = (ctypes.c_void_p * k)()
+    o = opt if opt is not None else hs_default_options()
+    _check(lib.hs_setup_batched(k, cp, om, nn, int(dim), int(pml_width), int(moving_pml_width), ctypes.byref(o),
+                                _stream(stream), out), "hs_setup_batched")
+    return [ctypes.c_void_p(out[q]) for q in range(k)]
+
+
+def hs_apply_batched(plans, rs, zs, nrhs, dtype, stream=None):
+    """z[k] = M_alpha^(k) r[k] for all plans in one (cached) CUDA graph."""
+    k = len(plans)
+    pp = (ctypes.c_void_p * k)(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    rp = (ctypes.c_void_p * k)(*[_ptr(r) for r in rs])
+    zp = (ctypes.c_void_p * k)(*[_ptr(z) for z in zs])
+    nr = (ctypes.c_int * k)(*[int(q) for q in nrhs])
+    return _check(load().hs_apply_batched(k, pp, rp, zp, nr, int(dtype), _stream(stream)), "hs_apply_batched")
+
+
+def hs_autotune(c, omega, n, dim, pml_width, moving_pml_width, nrhs, opt=None, stream=None):
+    """Time the candidate chunk lengths; returns (best chunk, ms per application)."""
+    lib = load()
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    o = opt if opt is not None else hs_default_options()
+    best, ms = ctypes.c_int(), ctypes.c_double()
+    _check(lib.hs_autotune(c.ctypes.data, float(omega), int(n), int(dim), int(pml_width), int(moving_pml_width),
+                           ctypes.byref(o), int(nrhs), _stream(stream), ctypes.byref(best), ctypes.byref(ms)),
+           "hs_autotune")
+    return best.value, ms.value
+
+
+def hs_kernel_launches():
+    return load().hs_kernel_launches()
+
+
+def hs_release_workspace():
+    return load().hs_release_workspace()
 
 
 def hs_apply(plan, r, z, nrhs, dtype, stream=None):

@@ -1,0 +1,170 @@
+"""Batching around the sweep (GPU): one-launch setup of problems of uneven n,
+concurrent applications as one CUDA graph, graph replay, the chunk-length
+autotuner and its cache, and bounded-wait failure reporting.
+
+The batched setup runs the same per-item code as the single-problem setup,
+and the graphs replay the same kernels, so their results must be bit-identical
+to the direct path; the direct path itself is held to the oracle.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import sweep2d as S
+from paper_1007_4291_gb300 import build as B
+from paper_1007_4291_gb300 import hs
+from paper_1007_4291_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+C_PML = 20.0
+BP = 6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    B.build()
+    return hs.load()
+
+
+def opts(**kw):
+    base = dict(alpha=2.0, pml_C=C_PML, layers_per_step=3, chunk=8, max_nrhs=4)
+    base.update(kw)
+    return hs.hs_default_options(**base)
+
+
+def omega_of(n):
+    return 2 * np.pi * (n + 1) / 16.0
+
+
+def relerr(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def apply_direct(plan, r, nrhs):
+    z = torch.empty_like(r)
+    hs.hs_apply(plan, r, z, nrhs, hs.HS_C64)
+    torch.cuda.synchronize()
+    assert hs.hs_last_device_status(plan) == hs.HS_OK
+    return z
+
+
+NS = [31, 45, 63, 47]   # uneven sizes in one batch
+
+
+def test_batched_setup_matches_single_setup_and_oracle():
+    cs = [I.random_velocity(n, 100 + k) for k, n in enumerate(NS)]
+    plans = hs.hs_setup_batched([c.ravel() for c in cs], [omega_of(n) for n in NS], NS, 2, BP, BP, opts())
+    singles = [hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(graphs=0)) for c, n in zip(cs, NS)]
+    try:
+        for k, n in enumerate(NS):
+            r = I.random_rhs(n, 2, 7 + k)
+            rg = torch.from_numpy(r).to("cuda").to(torch.complex64)
+            zb = apply_direct(plans[k], rg, 2).cpu().numpy()
+            zs = apply_direct(singles[k], rg, 2).cpu().numpy()
+            assert np.array_equal(zb, zs), n          # same per-item arithmetic
+            st = S.setup(cs[k], omega_of(n), BP, BP, 3, 2.0, C_PML)
+            ref = S.apply(st, r.astype(np.complex64).astype(np.complex128))
+            assert relerr(zb.astype(np.complex128), ref) <= 1e-4, n
+    finally:
+        for p in plans + singles:
+            hs.hs_destroy(p)
+
+
+def test_graph_replay_is_bit_identical_to_direct_launches():
+    n = 63
+    c = I.random_velocity(n, 3)
+    pg = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(graphs=1))
+    pd = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(graphs=0))
+    try:
+        for seed in (1, 2, 3):       # capture on the first call, replay after; new data each time
+            r = torch.from_numpy(I.random_rhs(n, 3, seed)).to("cuda").to(torch.complex64)
+            assert torch.equal(apply_direct(pg, r, 3), apply_direct(pd, r, 3))
+        r = torch.from_numpy(I.random_rhs(n, 1, 9)).to("cuda").to(torch.complex64)   # another nrhs
+        assert torch.equal(apply_direct(pg, r, 1), apply_direct(pd, r, 1))
+    finally:
+        hs.hs_destroy(pg)
+        hs.hs_destroy(pd)
+
+
+def test_apply_batched_matches_per_problem_applies():
+    cs = [I.random_velocity(n, 200 + k) for k, n in enumerate(NS)]
+    plans = hs.hs_setup_batched([c.ravel() for c in cs], [omega_of(n) for n in NS], NS, 2, BP, BP,
+                                opts(graphs=0))
+    try:
+        nr = [1, 3, 2, 4]
+        for call in range(3):        # capture, then two replays with fresh inputs
+            rs = [torch.from_numpy(I.random_rhs(n, q, 50 + 10 * call + k)).to("cuda").to(torch.complex64)
+                  for k, (n, q) in enumerate(zip(NS, nr))]
+            zs = [torch.empty_like(r) for r in rs]
+            hs.hs_apply_batched(plans, rs, zs, nr, hs.HS_C64)
+            torch.cuda.synchronize()
+            for k in range(len(NS)):
+                assert hs.hs_last_device_status(plans[k]) == hs.HS_OK
+                assert torch.equal(zs[k], apply_direct(plans[k], rs[k], nr[k])), (call, k)
+    finally:
+        for p in plans:
+            hs.hs_destroy(p)
+
+
+def test_apply_batched_rejects_repeated_plan_and_bad_nrhs():
+    n = 31
+    p = hs.hs_setup(I.constant_velocity(n).ravel(), omega_of(n), n, 2, BP, BP, opts())
+    try:
+        r = torch.zeros(4 * n * n, dtype=torch.complex64, device="cuda")
+        with pytest.raises(hs.HsError):
+            hs.hs_apply_batched([p, p], [r, r], [r, r], [1, 1], hs.HS_C64)
+        with pytest.raises(hs.HsError):
+            hs.hs_apply_batched([p], [r], [r], [5], hs.HS_C64)
+    finally:
+        hs.hs_destroy(p)
+
+
+def test_autotune_writes_cache_that_setup_reads(tmp_path):
+    n = 95
+    c = I.random_velocity(n, 5)
+    cache = str(tmp_path / "tune.txt")
+    o = opts(max_nrhs=2, chunk=0, tune_cache=cache)
+    best, ms = hs.hs_autotune(c.ravel(), omega_of(n), n, 2, BP, BP, 2, opt=o)
+    assert best >= 2 and ms > 0
+    line = open(cache).read().strip().splitlines()[-1]
+    assert ("n=%d" % n) in line and ("chunk=%d" % best) in line
+    # a setup with chunk = 0 and the cache gives the same operator as chunk = best
+    pt = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(max_nrhs=2, chunk=0, tune_cache=cache))
+    pe = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(max_nrhs=2, chunk=best))
+    try:
+        r = torch.from_numpy(I.random_rhs(n, 2, 4)).to("cuda").to(torch.complex64)
+        assert torch.equal(apply_direct(pt, r, 2), apply_direct(pe, r, 2))
+    finally:
+        hs.hs_destroy(pt)
+        hs.hs_destroy(pe)
+    os.remove(cache)
+
+
+def test_expired_device_wait_is_reported_and_context_stays_usable():
+    """A plan whose device waits may take one clock cycle: the first
+    shared-memory copy cannot land in time, every CTA gives up together,
+    drains its copies in flight, records HS_ETIMEOUT and exits; the host
+    reads the status, and the next plan still runs."""
+    n = 63
+    c = I.random_velocity(n, 8)
+    bad = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(spin_budget=1, graphs=0))
+    try:
+        r = torch.from_numpy(I.random_rhs(n, 2, 1)).to("cuda").to(torch.complex64)
+        z = torch.empty_like(r)
+        hs.hs_apply(bad, r, z, 2, hs.HS_C64)
+        assert hs.hs_sync(bad) == hs.HS_ETIMEOUT
+    finally:
+        hs.hs_destroy(bad)
+    good = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts())
+    try:
+        r = I.random_rhs(n, 2, 1)
+        z = apply_direct(good, torch.from_numpy(r).to("cuda").to(torch.complex64), 2).cpu().numpy()
+        ref = S.apply(S.setup(c, omega_of(n), BP, BP, 3, 2.0, C_PML), r.astype(np.complex64).astype(np.complex128))
+        assert relerr(z.astype(np.complex128), ref) <= 1e-4
+    finally:
+        hs.hs_destroy(good)
