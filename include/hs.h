@@ -57,8 +57,9 @@ typedef struct {
   int restart;           /* FGMRES restart length m.                                                  default 20 */
   int reorth;            /* 0: classical Gram-Schmidt; 1: CGS with a second pass when needed (DGKS).  default 0 */
   long long spin_budget; /* SM clock cycles a device-side barrier wait may take before HS_ETIMEOUT.   default 1<<30 */
-  int graphs;            /* 1: hs_apply and hs_solve replay the stage chain of the sweep as a CUDA
-                            graph (captured on first use per nrhs); 0: direct launches.          default 1 */
+  int graphs;            /* 1: hs_apply replays the stage chain of the sweep as a CUDA graph
+                            (captured on first use per nrhs); 0: direct launches.  hs_solve
+                            sweeps a different Krylov vector at every step and launches directly. default 1 */
   const char* tune_cache;/* path of the chunk-length table written by hs_autotune; with chunk = 0,
                             hs_setup takes the chunk length from it when it holds the problem's
                             key.  NULL: not used.  The string must outlive the hs_setup call.    default NULL */
@@ -76,6 +77,7 @@ typedef struct {
   double t_matvec_ms;    /* device time in A z products */
   double t_orth_ms;      /* device time in Gram-Schmidt and updates */
   double t_total_ms;     /* wall time of the call */
+  int cnn_applies;       /* applications that added the attached network's correction */
 } hs_solve_info;
 
 /* Fill *opt with the defaults listed above.  Returns HS_EINVAL if opt is NULL. */
@@ -197,6 +199,57 @@ int hs_matvec(hs_plan* plan, const void* x, void* y, int nrhs, int dtype, void* 
  */
 int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double tol, int maxit,
              hs_solve_info* info, void* stream);
+
+/*
+ * Convolutional post-correction of the sweep (no counterpart in the paper; a
+ * learned addition used inside flexible GMRES, judged by the FP64 residual).
+ * For a sweep output x = M_alpha r:
+ *
+ *   z <- z + s N(x / s),   s = sqrt(mean over points of |x|^2) per RHS,
+ *   N = conv3x3(2->32) + b1, ReLU, conv3x3(32->32) + b2, ReLU, conv3x3(32->2) + b3,
+ *
+ * on the n x n grid of each RHS (rows x2, columns x1, zero padding), input
+ * channels (Re, Im) of x/s, output channels (Re, Im) of the correction; it
+ * is trained on the sweep's error e = A^{-1} r - M_alpha r.
+ * Parameters: HS_CNN_NPARAM floats in the order W1[3][3][2][32], b1[32],
+ * W2[3][3][32][32], b2[32], W3[3][3][32][2], b3[2]; W[ky][kx][ci][co]
+ * multiplies input channel ci at row offset ky-1 and column offset kx-1.
+ * Activations are stored in bfloat16, weights used as their bfloat16
+ * roundings of FP32 masters; arithmetic in FP32.
+ */
+#define HS_CNN_NPARAM 10434
+typedef struct hs_cnn hs_cnn;
+
+/* Create a network from HOST parameters (copied).  */
+int hs_cnn_create(const float* params, hs_cnn** out);
+/* Copy the current FP32 parameters to HOST memory (HS_CNN_NPARAM floats). */
+int hs_cnn_get_params(const hs_cnn* net, float* params);
+/* 1: layer 2 on the tensor cores (tcgen05); 0: FP32 reference kernel. */
+int hs_cnn_set_mode(hs_cnn* net, int tensor_cores);
+/* z += s N(x / s) for nrhs device vectors of n x n points (ABI layout, dtype
+ * HS_C64 or HS_C128); x and z may alias (the usual use: z = x = M_alpha r).
+ * Workspace (two bf16 activation tensors of nrhs*n*n*32 values) is
+ * allocated on first use and kept. */
+int hs_cnn_apply(hs_cnn* net, const void* x, void* z, int nrhs, int n, int dtype, void* stream);
+/* Loss L = mean over points and RHS of |N(x/s) - e/s|^2 for training pairs
+ * (x, e) = (M_alpha r, A^{-1} r - M_alpha r) (device, ABI layout) and its
+ * gradient dL/dtheta (HOST, may be NULL).  Synchronises the stream. */
+int hs_cnn_gradient(hs_cnn* net, const void* x, const void* e, int nrhs, int n, int dtype, double* loss,
+                    float* grad, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
+ * gradient of the same loss; *loss (if not NULL) gets the loss before the
+ * step (synchronises the stream). */
+int hs_cnn_train_step(hs_cnn* net, const void* x, const void* e, int nrhs, int n, int dtype, double lr,
+                      double* loss, void* stream);
+/* Wait for `stream` and report a device error recorded by the network's
+ * tensor-core kernel (HS_ETIMEOUT after an expired bounded wait). */
+int hs_cnn_sync(hs_cnn* net, void* stream);
+int hs_cnn_destroy(hs_cnn* net);
+/* Let hs_solve use z = x + s N(x / s), x = M_alpha v, as its preconditioner
+ * (NULL detaches).  A restart cycle whose true FP64 residual does not fall below
+ * 0.9 of the previous cycle's switches the network off for the rest of that
+ * solve (plain sweep fallback).  The network must outlive its use. */
+int hs_attach_cnn(hs_plan* plan, hs_cnn* net);
 
 /* Wait for the plan's work on `stream` and report any recorded device error. */
 int hs_sync(hs_plan* plan, void* stream);

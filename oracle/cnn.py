@@ -1,18 +1,20 @@
 """FP64 reference of the convolutional post-correction of the sweep (oracle; test infrastructure only).
 
 The paper has no learned component.  This restates the small network the
-GPU path uses as a flexible-GMRES post-correction, z = M_alpha r + s N(r / s):
+GPU path uses as a flexible-GMRES post-correction of the sweep output
+x = M_alpha r:  z = x + s N(x / s):
 
-* s = rms(r) = sqrt(mean_x |r(x)|^2) per right-hand side (N is applied to a
+* s = rms(x) = sqrt(mean over points of |x|^2) per right-hand side (N sees a
   unit-scale input, and scaling r scales the correction: the preconditioner
-  stays positively homogeneous, as FGMRES wants of a linear preconditioner);
-* the input image has two channels (Re r / s, Im r / s) on the n x n grid,
+  stays positively homogeneous);
+* the input image has two channels (Re x / s, Im x / s) on the n x n grid,
   rows x2, columns x1;
 * N = conv3x3(2 -> 32) + bias, ReLU, conv3x3(32 -> 32) + bias, ReLU,
   conv3x3(32 -> 2) + bias; "same" size with zero padding; the output's two
   channels are the real and imaginary parts of the correction;
-* the training loss of pairs (r_k, e_k), e_k = A^{-1} r_k - M_alpha r_k, is
-  the mean over points and right-hand sides of |N(r_k/s_k) - e_k/s_k|^2;
+* the training loss of pairs (x_k, e_k), e_k = A^{-1} r_k - M_alpha r_k the
+  error of the sweep, is the mean over points and right-hand sides of
+  |N(x_k/s_k) - e_k/s_k|^2;
 * Adam (Kingma & Ba 2015) with bias correction updates the parameters.
 
 Parameter vector (float, this order): W1[3][3][2][32], b1[32],
@@ -114,7 +116,7 @@ def forward(theta, x, bf16=False):
 
 
 def correction(theta, r, bf16=False):
-    """s N(r / s) as a complex field (zero when r = 0)."""
+    """s N(r / s), s = rms(r), as a complex field (zero when r = 0); r is the sweep output."""
     s = rms(r)
     if s == 0.0:
         return np.zeros_like(np.asarray(r, dtype=np.complex128))

@@ -1,0 +1,638 @@
+// Convolutional post-correction of the sweep output x = M_alpha r:
+// z <- z + s N(x / s), s = rms(x) per right-hand side (x and z usually the
+// same vector), N = conv3x3(2->32)+ReLU, conv3x3(32->32)
+// +ReLU, conv3x3(32->2), zero padding, used as a flexible preconditioner in
+// FGMRES (the paper's method has no learned part; this is an addition whose
+// output the FP64 true residual judges, with the plain sweep as fallback).
+//
+// Storage: activations in bfloat16, NHWC ([rhs][x2][x1][channel]); weights
+// as FP32 masters with a bfloat16-rounded copy used by every forward kernel;
+// gradients and Adam moments in FP32.  Arithmetic is FP32.  The training
+// loss is the mean over points and RHS of |N(x/s) - e/s|^2, e the sweep's
+// error A^{-1} r - M_alpha r.  The kernels name the input r.
+//
+// The 32 -> 32 layer (89 % of the multiply-adds) runs as an implicit GEMM on
+// the fifth-generation tensor cores (hs_conv_tc.cu); this file holds the
+// two thin layers, the backward pass, Adam, and the host API.
+#include <algorithm>
+#include <cuda_bf16.h>
+#include "hs_internal.cuh"
+#include "hs_device.cuh"
+#include "hs_df64.cuh"
+#include "hs_cnn.cuh"
+
+namespace hs {
+namespace {
+
+// ------------------------------------------------------------------ vectors
+// Complex vector element (rhs k, point p) at base[p * sp + k * sk].
+__device__ __forceinline__ c128 ldc(const c64* b, long long i) { return c128{(double)b[i].re, (double)b[i].im}; }
+__device__ __forceinline__ c128 ldc(const c128* b, long long i) { return b[i]; }
+__device__ __forceinline__ c128 ldc(const cdf* b, long long i) {
+  const cdf v = b[i];
+  return c128{(double)v.re.h + (double)v.re.l, (double)v.im.h + (double)v.im.l};
+}
+__device__ __forceinline__ void addc(c64* b, long long i, double re, double im) {
+  b[i].re = (float)((double)b[i].re + re);
+  b[i].im = (float)((double)b[i].im + im);
+}
+__device__ __forceinline__ void addc(c128* b, long long i, double re, double im) {
+  b[i].re += re;
+  b[i].im += im;
+}
+
+// bfloat16 rounding of a double through float (round to nearest even twice)
+__device__ __forceinline__ float bf16r(double x) { return __bfloat162float(__float2bfloat16_rn(__double2float_rn(x))); }
+__device__ __forceinline__ float bf16f(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+template <typename T>
+__global__ void sumsq_kernel(const T* __restrict__ r, long long sp, long long sk, int n2, double* sums) {
+  const int k = blockIdx.y;
+  double acc = 0.0;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n2; p += (long long)gridDim.x * blockDim.x) {
+    const c128 v = ldc(r, p * sp + k * sk);
+    acc += v.re * v.re + v.im * v.im;
+  }
+  __shared__ double red[8];
+  for (int m = 16; m > 0; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(&sums[k], t);
+  }
+}
+
+__device__ __forceinline__ double inv_scale(const double* sums, int k, int n2) {
+  const double s2 = sums[k] / n2;
+  return s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+}
+
+// ------------------------------------------------------------------ layer 1
+// h1 = bf16(relu(b1 + W1 * x)), x = bf16(r / s); one thread per pixel.
+template <typename T>
+__global__ void __launch_bounds__(256) conv1_kernel(const T* __restrict__ r, long long sp, long long sk, int n,
+                                                   const double* sums, const float* __restrict__ wq,
+                                                   __nv_bfloat16* __restrict__ h1) {
+  __shared__ float w[CNN_W1 + CH];
+  for (int i = threadIdx.x; i < CNN_W1 + CH; i += blockDim.x) w[i] = wq[CNN_OFF_W1 + i];   // W1 then b1
+  __syncthreads();
+  const int k = blockIdx.y;
+  const int n2 = n * n;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n2) return;
+  const int i2 = p / n, i1 = p % n;
+  const double is = inv_scale(sums, k, n2);
+  float a[CH];
+#pragma unroll
+  for (int co = 0; co < CH; ++co) a[co] = w[CNN_W1 + co];
+#pragma unroll
+  for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) {
+      const int y = i2 + ky - 1, x = i1 + kx - 1;
+      float xr = 0.f, xi = 0.f;
+      if (y >= 0 && y < n && x >= 0 && x < n) {
+        const c128 v = ldc(r, (long long)(y * n + x) * sp + k * sk);
+        xr = bf16r(v.re * is);
+        xi = bf16r(v.im * is);
+      }
+      const float* wt = w + (ky * 3 + kx) * 2 * CH;
+#pragma unroll
+      for (int co = 0; co < CH; ++co) a[co] = fmaf(wt[co], xr, fmaf(wt[CH + co], xi, a[co]));
+    }
+  __nv_bfloat162 o[CH / 2];
+#pragma unroll
+  for (int c = 0; c < CH / 2; ++c) o[c] = __floats2bfloat162_rn(fmaxf(a[2 * c], 0.f), fmaxf(a[2 * c + 1], 0.f));
+  uint4* dst = reinterpret_cast<uint4*>(h1 + ((long long)k * n2 + p) * CH);
+  const uint4* src = reinterpret_cast<const uint4*>(o);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dst[q] = src[q];
+}
+
+// Load the (TH+2) x (TW+2) haloed tile of a 32-channel bf16 NHWC image
+// into shared memory as float [y][x][32] (zero outside the image).
+template <int TH, int TW>
+__device__ __forceinline__ void load_tile32(const __nv_bfloat16* __restrict__ img, int n, int y0, int x0,
+                                            float* tile) {
+  constexpr int HH = TH + 2, WW = TW + 2;
+  for (int i = threadIdx.x; i < HH * WW * 4; i += blockDim.x) {
+    const int q = i & 3, px = i >> 2;
+    const int ty = px / WW, tx = px % WW;
+    const int y = y0 + ty - 1, x = x0 + tx - 1;
+    float* d = tile + px * CH + q * 8;
+    if (y >= 0 && y < n && x >= 0 && x < n) {
+      const uint4 v = reinterpret_cast<const uint4*>(img + ((long long)y * n + x) * CH)[q];
+      const __nv_bfloat162* b = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float2 f = __bfloat1622float2(b[c]);
+        d[2 * c] = f.x;
+        d[2 * c + 1] = f.y;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) d[c] = 0.f;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ layer 2 (reference form)
+// h2 = bf16(relu(b2 + W2 * h1)) with FP32 FMAs: 16 x 16 pixel tiles, one
+// thread per pixel and 32 output channels.  Used for training and as the
+// cross-check of the tensor-core kernel.
+__global__ void __launch_bounds__(256) conv2_simt_kernel(const __nv_bfloat16* __restrict__ h1, int n,
+                                                         const float* __restrict__ wq, __nv_bfloat16* __restrict__ h2) {
+  extern __shared__ __align__(16) float sm[];
+  float* w = sm;                          // W2 [288][32] then b2 [32]
+  float* tile = sm + CNN_W2 + CH;         // [18][18][32]
+  const int k = blockIdx.z;
+  const int y0 = blockIdx.y * 16, x0 = blockIdx.x * 16;
+  for (int i = threadIdx.x; i < CNN_W2 + CH; i += blockDim.x) w[i] = wq[CNN_OFF_W2 + i];
+  load_tile32<16, 16>(h1 + (long long)k * n * n * CH, n, y0, x0, tile);
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  const int y = y0 + ty, x = x0 + tx;
+  float a[CH];
+#pragma unroll
+  for (int co = 0; co < CH; ++co) a[co] = w[CNN_W2 + co];
+  for (int ky = 0; ky < 3; ++ky)
+    for (int kx = 0; kx < 3; ++kx) {
+      const float* xin = tile + ((ty + ky) * 18 + tx + kx) * CH;
+      const float* wt = w + (ky * 3 + kx) * CH * CH;
+      for (int ci = 0; ci < CH; ++ci) {
+        const float xv = xin[ci];
+        const float4* w4 = reinterpret_cast<const float4*>(wt + ci * CH);
+#pragma unroll
+        for (int q = 0; q < CH / 4; ++q) {
+          const float4 v = w4[q];
+          a[4 * q] = fmaf(v.x, xv, a[4 * q]);
+          a[4 * q + 1] = fmaf(v.y, xv, a[4 * q + 1]);
+          a[4 * q + 2] = fmaf(v.z, xv, a[4 * q + 2]);
+          a[4 * q + 3] = fmaf(v.w, xv, a[4 * q + 3]);
+        }
+      }
+    }
+  if (y >= n || x >= n) return;
+  __nv_bfloat162 o[CH / 2];
+#pragma unroll
+  for (int c = 0; c < CH / 2; ++c) o[c] = __floats2bfloat162_rn(fmaxf(a[2 * c], 0.f), fmaxf(a[2 * c + 1], 0.f));
+  uint4* dst = reinterpret_cast<uint4*>(h2 + (((long long)k * n + y) * n + x) * CH);
+  const uint4* src = reinterpret_cast<const uint4*>(o);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dst[q] = src[q];
+}
+
+// ------------------------------------------------------------------ layer 3
+// o = b3 + W3 * h2.  APPLY: z += s (o0 + i o1).  TRAIN: d = o - e/s,
+// dL/do = 2 d / npts, loss += |d|^2 / npts.
+template <typename T, typename Z, bool TRAIN>
+__global__ void __launch_bounds__(256) conv3_kernel(const __nv_bfloat16* __restrict__ h2, int n, const float* __restrict__ wq,
+                                                   const double* sums, Z* z, long long sp, long long sk,
+                                                   const T* __restrict__ e, float* __restrict__ dout, double inv_npts,
+                                                   double* loss) {
+  extern __shared__ __align__(16) float sm[];
+  float* w = sm;                          // W3 [288][2] then b3 [2]
+  float* tile = sm + CNN_W3 + 2 + 2;      // [18][18][32] (16-byte aligned)
+  const int k = blockIdx.z;
+  const int y0 = blockIdx.y * 16, x0 = blockIdx.x * 16;
+  for (int i = threadIdx.x; i < CNN_W3 + 2; i += blockDim.x) w[i] = wq[CNN_OFF_W3 + i];
+  load_tile32<16, 16>(h2 + (long long)k * n * n * CH, n, y0, x0, tile);
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  const int y = y0 + ty, x = x0 + tx;
+  float o0 = w[CNN_W3], o1 = w[CNN_W3 + 1];
+  for (int ky = 0; ky < 3; ++ky)
+    for (int kx = 0; kx < 3; ++kx) {
+      const float* xin = tile + ((ty + ky) * 18 + tx + kx) * CH;
+      const float2* wt = reinterpret_cast<const float2*>(w + (ky * 3 + kx) * CH * 2);
+#pragma unroll 8
+      for (int ci = 0; ci < CH; ++ci) {
+        const float2 v = wt[ci];
+        o0 = fmaf(v.x, xin[ci], o0);
+        o1 = fmaf(v.y, xin[ci], o1);
+      }
+    }
+  const int n2 = n * n;
+  double l = 0.0;
+  if (y < n && x < n) {
+    const long long p = (long long)y * n + x;
+    const double is = inv_scale(sums, k, n2);
+    if (!TRAIN) {
+      if (is > 0.0) addc(z, p * sp + k * sk, (double)o0 / is, (double)o1 / is);
+    } else {
+      const c128 ev = ldc(e, p * sp + k * sk);
+      const float d0 = is > 0.0 ? o0 - (float)(ev.re * is) : 0.f;
+      const float d1 = is > 0.0 ? o1 - (float)(ev.im * is) : 0.f;
+      float2* dp = reinterpret_cast<float2*>(dout + ((long long)k * n2 + p) * 2);
+      *dp = make_float2((float)(2.0 * d0 * inv_npts), (float)(2.0 * d1 * inv_npts));
+      l = ((double)d0 * d0 + (double)d1 * d1) * inv_npts;
+    }
+  }
+  if (TRAIN) {
+    __shared__ double red[8];
+    for (int m = 16; m > 0; m >>= 1) l += __shfl_xor_sync(0xffffffffu, l, m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < 8; ++q) t += red[q];
+      atomicAdd(loss, t);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ backward, data
+// da[p][ci] = [h[p][ci] > 0] sum_{tap, co} W[tap][ci][co] dy[p - off(tap)][co]
+// (32 target channels; COUT = 2 for the last layer, 32 for the middle one).
+template <int COUT>
+__global__ void __launch_bounds__(256) bwd_data_kernel(const float* __restrict__ dy, int n,
+                                                      const float* __restrict__ wq, int woff,
+                                                      const __nv_bfloat16* __restrict__ h, float* __restrict__ da) {
+  extern __shared__ __align__(16) float sm[];
+  float* wt = sm;                          // [9][COUT][32]: transposed weights
+  float* tile = sm + 9 * COUT * CH;        // [18][18][COUT]
+  const int k = blockIdx.z;
+  const int y0 = blockIdx.y * 16, x0 = blockIdx.x * 16;
+  for (int i = threadIdx.x; i < 9 * CH * COUT; i += blockDim.x) {
+    const int tap = i / (CH * COUT), rem = i % (CH * COUT), ci = rem / COUT, co = rem % COUT;
+    wt[(tap * COUT + co) * CH + ci] = wq[woff + i];
+  }
+  for (int i = threadIdx.x; i < 18 * 18 * COUT; i += blockDim.x) {
+    const int c = i % COUT, px = i / COUT, ty = px / 18, tx = px % 18;
+    const int y = y0 + ty - 1, x = x0 + tx - 1;
+    tile[i] = (y >= 0 && y < n && x >= 0 && x < n) ? dy[(((long long)k * n + y) * n + x) * COUT + c] : 0.f;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  const int y = y0 + ty, x = x0 + tx;
+  if (y >= n || x >= n) return;
+  float a[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) a[c] = 0.f;
+  for (int ky = 0; ky < 3; ++ky)
+    for (int kx = 0; kx < 3; ++kx) {
+      // forward: y[q] uses x[q + off]; so x[p] feeds y[p - off]
+      const float* g = tile + ((ty + 2 - ky) * 18 + (tx + 2 - kx)) * COUT;
+      const float* w = wt + (ky * 3 + kx) * COUT * CH;
+      for (int co = 0; co < COUT; ++co) {
+        const float gv = g[co];
+        const float4* w4 = reinterpret_cast<const float4*>(w + co * CH);
+#pragma unroll
+        for (int q = 0; q < CH / 4; ++q) {
+          const float4 v = w4[q];
+          a[4 * q] = fmaf(v.x, gv, a[4 * q]);
+          a[4 * q + 1] = fmaf(v.y, gv, a[4 * q + 1]);
+          a[4 * q + 2] = fmaf(v.z, gv, a[4 * q + 2]);
+          a[4 * q + 3] = fmaf(v.w, gv, a[4 * q + 3]);
+        }
+      }
+    }
+  const long long p = ((long long)k * n + y) * n + x;
+  const uint4* hv = reinterpret_cast<const uint4*>(h + p * CH);
+  float4* out = reinterpret_cast<float4*>(da + p * CH);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint4 v = hv[q];
+    const __nv_bfloat162* b = reinterpret_cast<const __nv_bfloat162*>(&v);
+    float m[8];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float2 f = __bfloat1622float2(b[c]);
+      m[2 * c] = f.x > 0.f ? 1.f : 0.f;
+      m[2 * c + 1] = f.y > 0.f ? 1.f : 0.f;
+    }
+    out[2 * q] = make_float4(a[8 * q] * m[0], a[8 * q + 1] * m[1], a[8 * q + 2] * m[2], a[8 * q + 3] * m[3]);
+    out[2 * q + 1] = make_float4(a[8 * q + 4] * m[4], a[8 * q + 5] * m[5], a[8 * q + 6] * m[6], a[8 * q + 7] * m[7]);
+  }
+}
+
+// ------------------------------------------------------------------ backward, weights
+// dW[tap][ci][co] += sum_p x[p + off(tap)][ci] dy[p][co], db[co] += sum_p dy[p][co].
+// Persistent CTAs over 16 x 16 tiles; thread t owns (tap, ci) = t / CG and
+// COUT / CG output channels, accumulated in registers over all its tiles.
+// XSRC: 0 = bf16 NHWC image with CIN = 32, else the complex input (CIN = 2).
+template <int CIN, int COUT, typename T>
+__global__ void __launch_bounds__(288) bwd_weight_kernel(const __nv_bfloat16* __restrict__ ximg, const T* __restrict__ r,
+                                                        long long sp, long long sk, const double* sums,
+                                                        const float* __restrict__ dy, int n, int R,
+                                                        float* __restrict__ grad, int woff, int boff) {
+  constexpr int NPAIR = 9 * CIN;
+  constexpr int CG = (NPAIR >= 288) ? 1 : 288 / NPAIR;
+  constexpr int CPT = COUT / CG;
+  static_assert(CPT * CG == COUT, "channel split");
+  extern __shared__ __align__(16) float sm[];
+  float* xt = sm;                         // [18][18][CIN]
+  float* gt = sm + 18 * 18 * CIN;         // [16][16][COUT]
+  const int t = threadIdx.x;
+  const bool owner = t < NPAIR * CG;
+  const int pair = owner ? t / CG : 0, cg = owner ? t % CG : 0;
+  const int tap = pair / CIN, ci = pair % CIN, ky = tap / 3, kx = tap % 3;
+  const int co0 = cg * CPT;
+  float acc[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) acc[c] = 0.f;
+  float bacc = 0.f;
+  const int tw = (n + 15) / 16;
+  const long long ntiles = (long long)R * tw * tw;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int k = (int)(tile / ((long long)tw * tw));
+    const int rem = (int)(tile % ((long long)tw * tw));
+    const int y0 = (rem / tw) * 16, x0 = (rem % tw) * 16;
+    __syncthreads();
+    if constexpr (CIN == CH) {
+      load_tile32<16, 16>(ximg + (long long)k * n * n * CH, n, y0, x0, xt);
+    } else {
+      const double is = inv_scale(sums, k, n * n);
+      for (int i = t; i < 18 * 18; i += blockDim.x) {
+        const int ty = i / 18, tx = i % 18, y = y0 + ty - 1, x = x0 + tx - 1;
+        float xr = 0.f, xi = 0.f;
+        if (y >= 0 && y < n && x >= 0 && x < n) {
+          const c128 v = ldc(r, (long long)(y * n + x) * sp + k * sk);
+          xr = bf16r(v.re * is);
+          xi = bf16r(v.im * is);
+        }
+        xt[i * CIN] = xr;
+        xt[i * CIN + 1] = xi;
+      }
+    }
+    for (int i = t; i < 256 * COUT; i += blockDim.x) {
+      const int c = i % COUT, px = i / COUT, ty = px / 16, tx = px % 16;
+      const int y = y0 + ty, x = x0 + tx;
+      gt[i] = (y < n && x < n) ? dy[(((long long)k * n + y) * n + x) * COUT + c] : 0.f;
+    }
+    __syncthreads();
+    if (owner) {
+      for (int py = 0; py < 16; ++py)
+        for (int px = 0; px < 16; ++px) {
+          const float xv = xt[((py + ky) * 18 + px + kx) * CIN + ci];
+          const float* g = gt + (py * 16 + px) * COUT + co0;
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) acc[c] = fmaf(xv, g[c], acc[c]);
+        }
+    }
+    if (t < COUT)
+      for (int px = 0; px < 256; ++px) bacc += gt[px * COUT + t];
+  }
+  if (owner) {
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) atomicAdd(grad + woff + (tap * CIN + ci) * COUT + co0 + c, acc[c]);
+  }
+  if (t < COUT) atomicAdd(grad + boff + t, bacc);
+}
+
+// ------------------------------------------------------------------ Adam
+__global__ void adam_kernel(float* theta, float* wq, float* grad, float* m, float* v, int np, float lr, float c1,
+                            float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const float g = grad[i];
+  const float mi = 0.9f * m[i] + 0.1f * g;
+  const float vi = 0.999f * v[i] + 0.001f * g * g;
+  m[i] = mi;
+  v[i] = vi;
+  const float th = theta[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+  theta[i] = th;
+  wq[i] = bf16f(th);
+  grad[i] = 0.f;
+}
+
+__global__ void round_params_kernel(const float* theta, float* wq, int np) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < np) wq[i] = bf16f(theta[i]);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host
+int Cnn::reserve(int R, int n) {
+  const size_t px = (size_t)R * n * n;
+  if (px <= cap_px && R <= cap_r) return HS_OK;
+  cudaDeviceSynchronize();
+  cudaFree(h1); cudaFree(h2); cudaFree(sums);
+  h1 = h2 = nullptr; sums = nullptr;
+  cap_px = 0; cap_r = 0;
+  HS_CUDA_TRY(cudaMalloc(&h1, px * CH * sizeof(__nv_bfloat16)));
+  HS_CUDA_TRY(cudaMalloc(&h2, px * CH * sizeof(__nv_bfloat16)));
+  HS_CUDA_TRY(cudaMalloc(&sums, (R + 1) * sizeof(double)));
+  cap_px = px;
+  cap_r = R;
+  return HS_OK;
+}
+
+int Cnn::reserve_train(int R, int n) {
+  HS_TRY_INT(reserve(R, n));
+  const size_t px = (size_t)R * n * n;
+  if (da1 && px <= cap_train) return HS_OK;
+  cudaDeviceSynchronize();
+  cudaFree(dout); cudaFree(da2); cudaFree(da1);
+  dout = da2 = da1 = nullptr;
+  cap_train = 0;
+  HS_CUDA_TRY(cudaMalloc(&dout, px * 2 * sizeof(float)));
+  HS_CUDA_TRY(cudaMalloc(&da2, px * CH * sizeof(float)));
+  HS_CUDA_TRY(cudaMalloc(&da1, px * CH * sizeof(float)));
+  cap_train = px;
+  return HS_OK;
+}
+
+Cnn::~Cnn() {
+  void* ptrs[] = {theta, wq, grad, m, v, h1, h2, dout, da2, da1, sums, w2tc, status};
+  for (void* q : ptrs) if (q) cudaFree(q);
+}
+
+namespace {
+
+size_t conv2_smem() { return (size_t)(CNN_W2 + CH + 18 * 18 * CH) * sizeof(float); }
+size_t conv3_smem() { return (size_t)(CNN_W3 + 4 + 18 * 18 * CH) * sizeof(float); }
+template <int COUT> size_t bwd_data_smem() { return (size_t)(9 * COUT * CH + 18 * 18 * COUT) * sizeof(float); }
+template <int CIN, int COUT> size_t bwd_weight_smem() { return (size_t)(18 * 18 * CIN + 256 * COUT) * sizeof(float); }
+
+void set_cnn_attributes() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(conv2_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv2_smem());
+    cudaFuncSetAttribute(bwd_data_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_data_smem<32>());
+    cudaFuncSetAttribute(bwd_data_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_data_smem<2>());
+  });
+}
+
+template <typename T, typename Z, bool TRAIN>
+int forward_t(Cnn& c, const T* r, Z* z, long long sp, long long sk, int R, int n, const T* e, double inv_npts,
+              bool tensor_cores, cudaStream_t s) {
+  set_cnn_attributes();
+  const int n2 = n * n;
+  cudaMemsetAsync(c.sums, 0, (R + 1) * sizeof(double), s);
+  note_launch();
+  sumsq_kernel<T><<<dim3(std::min((n2 + 255) / 256, 64), R), 256, 0, s>>>(r, sp, sk, n2, c.sums);
+  note_launch();
+  conv1_kernel<T><<<dim3((n2 + 255) / 256, R), 256, 0, s>>>(r, sp, sk, n, c.sums, c.wq, c.h1);
+  const dim3 tiles((n + 15) / 16, (n + 15) / 16, R);
+  if (tensor_cores) {
+    HS_TRY_INT(conv2_tc(c, R, n, s));
+  } else {
+    note_launch();
+    conv2_simt_kernel<<<tiles, 256, conv2_smem(), s>>>(c.h1, n, c.wq, c.h2);
+  }
+  note_launch();
+  conv3_kernel<T, Z, TRAIN><<<tiles, 256, conv3_smem(), s>>>(c.h2, n, c.wq, c.sums, z, sp, sk, e, c.dout, inv_npts,
+                                                              c.sums + R);
+  cudaError_t ce = cudaGetLastError();
+  return ce == cudaSuccess ? HS_OK : cuda_status(ce);
+}
+
+template <typename T>
+int gradient_t(Cnn& c, const T* r, const T* e, long long sp, long long sk, int R, int n, cudaStream_t s) {
+  HS_TRY_INT(c.reserve_train(R, n));
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(bwd_weight_kernel<CH, CH, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwd_weight_smem<CH, CH>());
+  });
+  cudaMemsetAsync(c.grad, 0, CNN_NPARAM * sizeof(float), s);
+  const double inv_npts = 1.0 / ((double)R * n * n);
+  HS_TRY_INT((forward_t<T, c64, true>(c, r, nullptr, sp, sk, R, n, e, inv_npts, false, s)));
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int gw = 2 * sms;
+  const dim3 tiles((n + 15) / 16, (n + 15) / 16, R);
+  note_launch(5);
+  bwd_weight_kernel<CH, 2, T><<<gw, 288, bwd_weight_smem<CH, 2>(), s>>>(c.h2, r, sp, sk, c.sums, c.dout, n, R, c.grad,
+                                                                      CNN_OFF_W3, CNN_OFF_W3 + CNN_W3);
+  bwd_data_kernel<2><<<tiles, 256, bwd_data_smem<2>(), s>>>(c.dout, n, c.wq, CNN_OFF_W3, c.h2, c.da2);
+  bwd_weight_kernel<CH, CH, T><<<gw, 288, bwd_weight_smem<CH, CH>(), s>>>(c.h1, r, sp, sk, c.sums, c.da2, n, R,
+                                                                        c.grad, CNN_OFF_W2, CNN_OFF_W2 + CNN_W2);
+  bwd_data_kernel<CH><<<tiles, 256, bwd_data_smem<CH>(), s>>>(c.da2, n, c.wq, CNN_OFF_W2, c.h1, c.da1);
+  bwd_weight_kernel<2, CH, T><<<gw, 288, bwd_weight_smem<2, CH>(), s>>>(nullptr, r, sp, sk, c.sums, c.da1, n, R,
+                                                                       c.grad, CNN_OFF_W1, CNN_OFF_W1 + CNN_W1);
+  cudaError_t ce = cudaGetLastError();
+  return ce == cudaSuccess ? HS_OK : cuda_status(ce);
+}
+
+int check_dims(int nrhs, int n, int dtype) {
+  if (nrhs < 1 || n < 1 || n > 65535 || (dtype != HS_C64 && dtype != HS_C128)) return HS_EINVAL;
+  return HS_OK;
+}
+
+}  // namespace
+
+// Correction inside the solver: z += s N(z/s) in place on the sweep output
+// in the internal layout (element (k, p) at p * R + k).  Safe in place: the
+// first layer reads all of z before the last one writes it (stream order).
+int cnn_correct(Cnn& c, void* z, int ztype, int R, int n, cudaStream_t s) {
+  HS_TRY_INT(c.reserve(R, n));
+  const long long sp = R, sk = 1;
+  if (ztype == HS_C64)
+    return forward_t<c64, c64, false>(c, (const c64*)z, (c64*)z, sp, sk, R, n, nullptr, 0.0, c.tensor_cores, s);
+  if (ztype == HS_C128)
+    return forward_t<c128, c128, false>(c, (const c128*)z, (c128*)z, sp, sk, R, n, nullptr, 0.0, c.tensor_cores, s);
+  return HS_EINVAL;
+}
+
+}  // namespace hs
+
+using namespace hs;
+
+extern "C" int hs_cnn_create(const float* params, hs_cnn** out) {
+  if (!params || !out) return HS_EINVAL;
+  *out = nullptr;
+  Cnn* c = new Cnn();
+  const size_t b = CNN_NPARAM * sizeof(float);
+  if (cudaMalloc(&c->theta, b) != cudaSuccess || cudaMalloc(&c->wq, b) != cudaSuccess ||
+      cudaMalloc(&c->grad, b) != cudaSuccess || cudaMalloc(&c->m, b) != cudaSuccess ||
+      cudaMalloc(&c->v, b) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return HS_ENOMEM;
+  }
+  cudaMemcpy(c->theta, params, b, cudaMemcpyHostToDevice);
+  cudaMemset(c->grad, 0, b);
+  cudaMemset(c->m, 0, b);
+  cudaMemset(c->v, 0, b);
+  note_launch();
+  round_params_kernel<<<(CNN_NPARAM + 255) / 256, 256>>>(c->theta, c->wq, CNN_NPARAM);
+  if (cudaDeviceSynchronize() != cudaSuccess) { delete c; return HS_ECUDA; }
+  *out = reinterpret_cast<hs_cnn*>(c);
+  return HS_OK;
+}
+
+extern "C" int hs_cnn_get_params(const hs_cnn* net, float* params) {
+  if (!net || !params) return HS_EINVAL;
+  const Cnn* c = reinterpret_cast<const Cnn*>(net);
+  HS_CUDA_TRY(cudaMemcpy(params, c->theta, CNN_NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+  return HS_OK;
+}
+
+extern "C" int hs_cnn_set_mode(hs_cnn* net, int tensor_cores) {
+  if (!net) return HS_EINVAL;
+  reinterpret_cast<Cnn*>(net)->tensor_cores = tensor_cores != 0;
+  return HS_OK;
+}
+
+extern "C" int hs_cnn_apply(hs_cnn* net, const void* r, void* z, int nrhs, int n, int dtype, void* stream) {
+  if (!net || !r || !z) return HS_EINVAL;
+  HS_TRY_INT(check_dims(nrhs, n, dtype));
+  Cnn& c = *reinterpret_cast<Cnn*>(net);
+  HS_TRY_INT(c.reserve(nrhs, n));
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long sp = 1, sk = (long long)n * n;
+  if (dtype == HS_C64)
+    return forward_t<c64, c64, false>(c, (const c64*)r, (c64*)z, sp, sk, nrhs, n, nullptr, 0.0, c.tensor_cores, s);
+  return forward_t<c128, c128, false>(c, (const c128*)r, (c128*)z, sp, sk, nrhs, n, nullptr, 0.0, c.tensor_cores, s);
+}
+
+extern "C" int hs_cnn_gradient(hs_cnn* net, const void* r, const void* e, int nrhs, int n, int dtype, double* loss,
+                               float* grad, void* stream) {
+  if (!net || !r || !e) return HS_EINVAL;
+  HS_TRY_INT(check_dims(nrhs, n, dtype));
+  Cnn& c = *reinterpret_cast<Cnn*>(net);
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long sp = 1, sk = (long long)n * n;
+  int st = (dtype == HS_C64) ? gradient_t<c64>(c, (const c64*)r, (const c64*)e, sp, sk, nrhs, n, s)
+                             : gradient_t<c128>(c, (const c128*)r, (const c128*)e, sp, sk, nrhs, n, s);
+  if (st != HS_OK) return st;
+  HS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (loss) HS_CUDA_TRY(cudaMemcpy(loss, c.sums + nrhs, sizeof(double), cudaMemcpyDeviceToHost));
+  if (grad) HS_CUDA_TRY(cudaMemcpy(grad, c.grad, CNN_NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+  return HS_OK;
+}
+
+extern "C" int hs_cnn_train_step(hs_cnn* net, const void* r, const void* e, int nrhs, int n, int dtype, double lr,
+                                 double* loss, void* stream) {
+  if (!net || !r || !e || !(lr > 0.0)) return HS_EINVAL;
+  HS_TRY_INT(check_dims(nrhs, n, dtype));
+  Cnn& c = *reinterpret_cast<Cnn*>(net);
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long sp = 1, sk = (long long)n * n;
+  int st = (dtype == HS_C64) ? gradient_t<c64>(c, (const c64*)r, (const c64*)e, sp, sk, nrhs, n, s)
+                             : gradient_t<c128>(c, (const c128*)r, (const c128*)e, sp, sk, nrhs, n, s);
+  if (st != HS_OK) return st;
+  c.t += 1;
+  const float c1 = (float)(1.0 - std::pow(0.9, c.t)), c2 = (float)(1.0 - std::pow(0.999, c.t));
+  note_launch();
+  adam_kernel<<<(CNN_NPARAM + 255) / 256, 256, 0, s>>>(c.theta, c.wq, c.grad, c.m, c.v, CNN_NPARAM, (float)lr, c1, c2);
+  if (loss) {
+    HS_CUDA_TRY(cudaMemcpyAsync(loss, c.sums + nrhs, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HS_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  cudaError_t ce = cudaGetLastError();
+  return ce == cudaSuccess ? HS_OK : cuda_status(ce);
+}
+
+extern "C" int hs_cnn_sync(hs_cnn* net, void* stream) {
+  if (!net) return HS_EINVAL;
+  Cnn& c = *reinterpret_cast<Cnn*>(net);
+  HS_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  if (!c.status) return HS_OK;
+  int st[3] = {0, 0, 0};
+  HS_CUDA_TRY(cudaMemcpy(st, c.status, sizeof(st), cudaMemcpyDeviceToHost));
+  return st[0];
+}
+
+extern "C" int hs_cnn_destroy(hs_cnn* net) {
+  if (!net) return HS_OK;
+  cudaDeviceSynchronize();
+  delete reinterpret_cast<Cnn*>(net);
+  return HS_OK;
+}

@@ -108,6 +108,7 @@ struct Plan {
   long long bytes = 0;
   long long uid = 0;        // process-unique id (keys of cached CUDA graphs)
   void* graphs = nullptr;   // cached executable graphs of this plan's sweep (hs_sweep.cu)
+  void* cnn = nullptr;      // attached post-correction network (hs_cnn.cuh), not owned
 };
 
 // ---------------------------------------------------------------- helpers

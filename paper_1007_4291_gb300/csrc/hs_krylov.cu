@@ -25,6 +25,7 @@
 #include <vector>
 #include "hs_internal.cuh"
 #include "hs_df64.cuh"
+#include "hs_cnn.cuh"
 
 namespace hs {
 namespace {
@@ -524,8 +525,11 @@ int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs
   std::vector<zc> H((size_t)R * (m + 1) * m), g((size_t)R * (m + 1)), sn((size_t)R * m);
   std::vector<double> cs((size_t)R * m), relres(R, 1.0), scl(R);
   std::vector<char> active(R);
-  int it = 0, cycles = 0, applies = 0;
+  int it = 0, cycles = 0, applies = 0, cnn_applies = 0;
   void* const u_saved = p.d_u;
+  Cnn* net = static_cast<Cnn*>(p.cnn);
+  bool cnn_on = net != nullptr;
+  double prev_cycle_res = HUGE_VAL;
   while (true) {
     // true residual r = f - A x -> V_0
     K.matvec(x, true, Vb, fi);
@@ -541,6 +545,12 @@ int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs
       g[(size_t)r * (m + 1)] = active[r] ? beta : 0.0;
       for (int q = 1; q <= m; ++q) g[(size_t)r * (m + 1) + q] = 0.0;
     }
+    // the FP64 true residual judges the learned correction: a cycle that
+    // did not reduce it below 0.9 of the previous one ends its use
+    double cycle_res = 0.0;
+    for (int r = 0; r < R; ++r) cycle_res = std::max(cycle_res, relres[r]);
+    if (cnn_on && cycles > 0 && !(cycle_res < 0.9 * prev_cycle_res)) cnn_on = false;
+    prev_cycle_res = cycle_res;
     if (all || it >= maxit) break;
     ++cycles;
     K.scale(Vb, scl, Vb);
@@ -559,7 +569,11 @@ int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs
         cudaMemcpyAsync(Zj2, Vj, vs * sizeof(c128), cudaMemcpyDeviceToDevice, s);
         p.d_u = Zj2;
       }
-      st = sweep_internal(p, R, s, p.opt.graphs != 0);
+      st = sweep_internal(p, R, s);   // z_j moves with j: direct launches
+      if (st == HS_OK && cnn_on) {      // z_j += s N(z_j / s), post-correction of the sweep output
+        st = cnn_correct(*net, p.d_u, p.prec, R, p.n, s);
+        ++cnn_applies;
+      }
       void* zj = p.d_u;
       p.d_u = u_saved;
       if (st != HS_OK) break;
@@ -659,6 +673,7 @@ int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs
     info->t_matvec_ms = t_mv;
     info->t_orth_ms = t_orth;
     info->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    info->cnn_applies = cnn_applies;
   }
   if (st == HS_OK && (mx > tol || nan)) st = HS_ENOCONV;
   return st;
@@ -677,6 +692,12 @@ extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double 
   cudaStream_t s = (cudaStream_t)stream;
   return (p.prec == HS_C64) ? solve_t<DF64>(p, f, u, nrhs, tol, maxit, info, s)
                             : solve_t<F64>(p, f, u, nrhs, tol, maxit, info, s);
+}
+
+extern "C" int hs_attach_cnn(hs_plan* plan, hs_cnn* net) {
+  if (!plan) return HS_EINVAL;
+  reinterpret_cast<Plan*>(plan)->cnn = net;
+  return HS_OK;
 }
 
 extern "C" int hs_release_workspace(void) {

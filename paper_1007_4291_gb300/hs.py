@@ -20,7 +20,10 @@ HS_C64, HS_C128 = 64, 128
 
 EXPORTED = ["hs_default_options", "hs_setup", "hs_setup_batched", "hs_apply", "hs_apply_batched",
             "hs_apply_noalloc", "hs_autotune", "hs_matvec", "hs_solve", "hs_sync", "hs_last_device_status",
-            "hs_plan_bytes", "hs_release_workspace", "hs_kernel_launches", "hs_destroy", "hs_strerror"]
+            "hs_plan_bytes", "hs_release_workspace", "hs_kernel_launches", "hs_destroy", "hs_strerror",
+            "hs_cnn_create", "hs_cnn_get_params", "hs_cnn_set_mode", "hs_cnn_apply", "hs_cnn_gradient",
+            "hs_cnn_train_step", "hs_cnn_sync", "hs_cnn_destroy", "hs_attach_cnn"]
+HS_CNN_NPARAM = 10434
 
 
 class HsOptions(ctypes.Structure):
@@ -33,7 +36,8 @@ class HsOptions(ctypes.Structure):
 class HsSolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("applies", ctypes.c_int),
                 ("max_relres", ctypes.c_double), ("t_apply_ms", ctypes.c_double),
-                ("t_matvec_ms", ctypes.c_double), ("t_orth_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double)]
+                ("t_matvec_ms", ctypes.c_double), ("t_orth_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double),
+                ("cnn_applies", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,6 +80,15 @@ def load(path=None):
     lib.hs_strerror.argtypes = [i]
     lib.hs_strerror.restype = ctypes.c_char_p
     lib.hs_release_workspace.argtypes = []
+    lib.hs_cnn_create.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.hs_cnn_get_params.argtypes = [vp, vp]
+    lib.hs_cnn_set_mode.argtypes = [vp, i]
+    lib.hs_cnn_apply.argtypes = [vp, vp, vp, i, i, i, vp]
+    lib.hs_cnn_gradient.argtypes = [vp, vp, vp, i, i, i, ctypes.POINTER(d), vp, vp]
+    lib.hs_cnn_train_step.argtypes = [vp, vp, vp, i, i, i, d, ctypes.POINTER(d), vp]
+    lib.hs_cnn_destroy.argtypes = [vp]
+    lib.hs_cnn_sync.argtypes = [vp, vp]
+    lib.hs_attach_cnn.argtypes = [vp, vp]
     lib.hs_kernel_launches.argtypes = []
     lib.hs_kernel_launches.restype = ll
     for name in EXPORTED:
@@ -182,6 +195,59 @@ def hs_autotune(c, omega, n, dim, pml_width, moving_pml_width, nrhs, opt=None, s
                            ctypes.byref(o), int(nrhs), _stream(stream), ctypes.byref(best), ctypes.byref(ms)),
            "hs_autotune")
     return best.value, ms.value
+
+
+def hs_cnn_create(params):
+    """Network from a host parameter vector (HS_CNN_NPARAM values)."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != HS_CNN_NPARAM:
+        raise ValueError("expected %d parameters" % HS_CNN_NPARAM)
+    net = ctypes.c_void_p()
+    _check(load().hs_cnn_create(p.ctypes.data, ctypes.byref(net)), "hs_cnn_create")
+    return net
+
+
+def hs_cnn_get_params(net):
+    out = np.empty(HS_CNN_NPARAM, dtype=np.float32)
+    _check(load().hs_cnn_get_params(net, out.ctypes.data), "hs_cnn_get_params")
+    return out
+
+
+def hs_cnn_set_mode(net, tensor_cores):
+    return _check(load().hs_cnn_set_mode(net, int(bool(tensor_cores))), "hs_cnn_set_mode")
+
+
+def hs_cnn_apply(net, r, z, nrhs, n, dtype, stream=None):
+    return _check(load().hs_cnn_apply(net, _ptr(r), _ptr(z), int(nrhs), int(n), int(dtype), _stream(stream)),
+                  "hs_cnn_apply")
+
+
+def hs_cnn_gradient(net, r, e, nrhs, n, dtype, stream=None):
+    """Returns (loss, gradient as a float32 host array)."""
+    loss = ctypes.c_double()
+    g = np.empty(HS_CNN_NPARAM, dtype=np.float32)
+    _check(load().hs_cnn_gradient(net, _ptr(r), _ptr(e), int(nrhs), int(n), int(dtype), ctypes.byref(loss),
+                                  g.ctypes.data, _stream(stream)), "hs_cnn_gradient")
+    return loss.value, g
+
+
+def hs_cnn_train_step(net, r, e, nrhs, n, dtype, lr, stream=None):
+    loss = ctypes.c_double()
+    _check(load().hs_cnn_train_step(net, _ptr(r), _ptr(e), int(nrhs), int(n), int(dtype), float(lr),
+                                    ctypes.byref(loss), _stream(stream)), "hs_cnn_train_step")
+    return loss.value
+
+
+def hs_cnn_sync(net, stream=None):
+    return load().hs_cnn_sync(net, _stream(stream))
+
+
+def hs_cnn_destroy(net):
+    return load().hs_cnn_destroy(net)
+
+
+def hs_attach_cnn(plan, net):
+    return _check(load().hs_attach_cnn(plan, net), "hs_attach_cnn")
 
 
 def hs_kernel_launches():

@@ -19,7 +19,7 @@ indexed [x_d, ..., x_1] with x_1 fastest.
 import numpy as np
 
 __all__ = ["random_velocity", "lens_velocity", "constant_velocity", "point_sources",
-           "centered_source", "random_rhs"]
+           "centered_source", "random_rhs", "cnn_init_params"]
 
 
 def _grid(n):
@@ -102,3 +102,17 @@ def random_rhs(n, nrhs, seed, dim=2):
     rng = np.random.default_rng(seed)
     shape = (nrhs,) + (n,) * dim
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def cnn_init_params(seed, out_scale=0.1):
+    """Initial parameters of the post-correction network (float32, flat layout
+    W1[3][3][2][32], b1, W2[3][3][32][32], b2, W3[3][3][32][2], b3): He-normal
+    weights (std sqrt(2 / fan_in), fan_in = 9 * input channels), zero biases,
+    the last layer scaled by ``out_scale`` so that training starts near the
+    plain sweep."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for cin, cout, scale in ((2, 32, 1.0), (32, 32, 1.0), (32, 2, out_scale)):
+        w = rng.standard_normal((3, 3, cin, cout)) * np.sqrt(2.0 / (9 * cin)) * scale
+        parts += [w.ravel(), np.zeros(cout)]
+    return np.concatenate(parts).astype(np.float32)

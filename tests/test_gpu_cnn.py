@@ -1,0 +1,173 @@
+"""GPU parity of the convolutional post-correction against its FP64 oracle.
+
+The oracle is run with bfloat16 rounding of weights and stored activations
+(the kernels' storage precision) and float64 arithmetic; the kernels use FP32
+arithmetic.  What remains is FP32 accumulation order and rare bf16 rounding
+flips of single activations, far below the tolerances:
+* forward correction: relative L2 <= 1e-3;
+* loss: relative 1e-4; gradient: relative L2 per parameter tensor <= 2e-3.
+"""
+import numpy as np
+import pytest
+
+from oracle import cnn as K
+from paper_1007_4291_gb300 import build as B
+from paper_1007_4291_gb300 import hs
+from paper_1007_4291_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    B.build()
+    return hs.load()
+
+
+def relerr(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def theta32(seed, out_scale=1.0):
+    return I.cnn_init_params(seed, out_scale=out_scale)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("n,R,dtype", [(37, 2, hs.HS_C64), (16, 1, hs.HS_C128), (53, 3, hs.HS_C64)])
+def test_forward_matches_oracle(n, R, dtype, mode):
+    th = theta32(1)
+    net = hs.hs_cnn_create(th)
+    try:
+        if mode == 1:
+            hs.hs_cnn_set_mode(net, 1)
+        r = I.random_rhs(n, R, 3) * 1e-3         # the network sees r / rms(r)
+        z0 = I.random_rhs(n, R, 4)
+        tdt = torch.complex64 if dtype == hs.HS_C64 else torch.complex128
+        rg = torch.from_numpy(r).to("cuda").to(tdt)
+        zg = torch.from_numpy(z0).to("cuda").to(tdt)
+        zin = zg.cpu().numpy().astype(np.complex128)
+        hs.hs_cnn_apply(net, rg, zg, R, n, dtype)
+        assert hs.hs_cnn_sync(net) == hs.HS_OK
+        got = zg.cpu().numpy().astype(np.complex128) - zin
+        rin = rg.cpu().numpy().astype(np.complex128)
+        for k in range(R):
+            ref = K.correction(th.astype(np.float64), rin[k], bf16=True)
+            assert relerr(got[k], ref) <= 1e-3, (k, relerr(got[k], ref))
+    finally:
+        hs.hs_cnn_destroy(net)
+
+
+def test_zero_input_gives_zero_correction():
+    net = hs.hs_cnn_create(theta32(2))
+    try:
+        n = 20
+        r = torch.zeros(2 * n * n, dtype=torch.complex64, device="cuda")
+        z = torch.ones_like(r)
+        hs.hs_cnn_apply(net, r, z, 2, n, hs.HS_C64)
+        assert torch.equal(z, torch.ones_like(r))
+    finally:
+        hs.hs_cnn_destroy(net)
+
+
+@pytest.mark.parametrize("n,R", [(21, 2), (40, 1)])
+def test_gradient_matches_oracle(n, R):
+    th = theta32(5)
+    net = hs.hs_cnn_create(th)
+    try:
+        r = I.random_rhs(n, R, 6)
+        e = 0.3 * I.random_rhs(n, R, 7)
+        rg = torch.from_numpy(r).to("cuda").to(torch.complex64)
+        eg = torch.from_numpy(e).to("cuda").to(torch.complex64)
+        loss, g = hs.hs_cnn_gradient(net, rg, eg, R, n, hs.HS_C64)
+        rin = rg.cpu().numpy().astype(np.complex128)
+        ein = eg.cpu().numpy().astype(np.complex128)
+        L, gref = K.loss_and_grad(th.astype(np.float64), list(rin), list(ein), bf16=True)
+        assert abs(loss - L) <= 1e-4 * L
+        gp, rp = K.unpack(g.astype(np.float64)), K.unpack(gref)
+        for name, _ in K.SHAPES:
+            assert relerr(gp[name], rp[name]) <= 2e-3, (name, relerr(gp[name], rp[name]))
+    finally:
+        hs.hs_cnn_destroy(net)
+
+
+def test_first_adam_step_moves_each_parameter_by_lr():
+    th = theta32(8)
+    net = hs.hs_cnn_create(th)
+    try:
+        n, R, lr = 24, 2, 1e-3
+        rg = torch.from_numpy(I.random_rhs(n, R, 1)).to("cuda").to(torch.complex64)
+        eg = torch.from_numpy(I.random_rhs(n, R, 2)).to("cuda").to(torch.complex64)
+        _, g = hs.hs_cnn_gradient(net, rg, eg, R, n, hs.HS_C64)
+        hs.hs_cnn_train_step(net, rg, eg, R, n, hs.HS_C64, lr)
+        th1 = hs.hs_cnn_get_params(net)
+        big = np.abs(g) > 1e-4
+        d = (th1 - th).astype(np.float64)
+        assert np.allclose(d[big], -lr * np.sign(g[big]), rtol=1e-2, atol=0)
+    finally:
+        hs.hs_cnn_destroy(net)
+
+
+def test_training_learns_a_teacher_network():
+    """The student (another random init) fits a teacher's corrections."""
+    n, R = 32, 8
+    teacher = theta32(11).astype(np.float64)
+    r = I.random_rhs(n, R, 12)
+    e = np.stack([K.correction(teacher, r[k], bf16=False) for k in range(R)])
+    rg = torch.from_numpy(r).to("cuda").to(torch.complex64)
+    eg = torch.from_numpy(e).to("cuda").to(torch.complex64)
+    net = hs.hs_cnn_create(theta32(13, out_scale=0.1))
+    try:
+        losses = [hs.hs_cnn_train_step(net, rg, eg, R, n, hs.HS_C64, 3e-3) for _ in range(150)]
+        assert np.mean(losses[-10:]) < 0.3 * losses[0], (losses[0], losses[-10:])
+    finally:
+        hs.hs_cnn_destroy(net)
+
+
+def test_solve_with_attached_network_reaches_tolerance():
+    """FGMRES with z = M v + s N(v/s): the FP64 true residual still decides;
+    an untrained (harmful) network is switched off and the solve converges."""
+    from oracle import helmholtz2d as H
+    n, bp = 63, 8
+    c = I.random_velocity(n, 2)
+    omega = 2 * np.pi * 4.0
+    R = 3
+    o = hs.hs_default_options(alpha=2.0, pml_C=20.0, layers_per_step=1, chunk=16, max_nrhs=R, restart=10)
+    plan = hs.hs_setup(c.ravel(), omega, n, 2, bp, bp, o)
+    net = hs.hs_cnn_create(theta32(3, out_scale=1.0))
+    try:
+        hs.hs_attach_cnn(plan, net)
+        f = I.point_sources(n, R, 1, bp)
+        fg = torch.from_numpy(f).to("cuda")
+        ug = torch.zeros_like(fg)
+        code, info = hs.hs_solve(plan, fg, ug, R, 1e-6, 300)
+        assert code == hs.HS_OK, info
+        assert info["cnn_applies"] > 0
+        A0 = H.helmholtz_matrix(c, omega, bp, 20.0, 0.0)
+        u = ug.cpu().numpy()
+        for k in range(R):
+            assert np.linalg.norm(f[k].ravel() - A0 @ u[k].ravel()) <= 1e-6 * np.linalg.norm(f[k].ravel())
+    finally:
+        hs.hs_destroy(plan)
+        hs.hs_cnn_destroy(net)
+
+
+def test_trained_network_reduces_heldout_sweep_error():
+    """Pairs made by the method (e = A^{-1} r - M r, A^{-1} by hs_solve) on
+    seeded n = 63 fields; after training, the corrected preconditioner's error
+    on a held-out field is below the plain sweep's (which scores 1)."""
+    from paper_1007_4291_gb300 import train_cnn as T
+    n = 63
+    r, e = T.make_pairs(n, [1000, 1001, 1002], 8, bp=8, b=8, layers=4)
+    rv, ev = T.make_pairs(n, [5000], 8, bp=8, b=8, layers=4)
+    net = hs.hs_cnn_create(I.cnn_init_params(0))
+    try:
+        before = T.corrected_error(net, rv, ev, n)
+        T.train(net, r, e, n, steps=300, batch=8, lr=1e-3)
+        after = T.corrected_error(net, rv, ev, n)
+        print("held-out relative squared error: plain 1.0, init %.4f, trained %.4f" % (before, after))
+        assert after < 1.0 and after < before
+    finally:
+        hs.hs_cnn_destroy(net)
