@@ -77,7 +77,7 @@ typedef struct {
   double t_matvec_ms;    /* device time in A z products */
   double t_orth_ms;      /* device time in Gram-Schmidt and updates */
   double t_total_ms;     /* wall time of the call */
-  int cnn_applies;       /* applications that added the attached network's correction */
+  int cnn_applies;       /* (direction, RHS) pairs for which the judge kept the network's correction */
 } hs_solve_info;
 
 /* Fill *opt with the defaults listed above.  Returns HS_EINVAL if opt is NULL. */
@@ -245,10 +245,12 @@ int hs_cnn_train_step(hs_cnn* net, const void* x, const void* e, int nrhs, int n
  * tensor-core kernel (HS_ETIMEOUT after an expired bounded wait). */
 int hs_cnn_sync(hs_cnn* net, void* stream);
 int hs_cnn_destroy(hs_cnn* net);
-/* Let hs_solve use z = x + s N(x / s), x = M_alpha v, as its preconditioner
- * (NULL detaches).  A restart cycle whose true FP64 residual does not fall below
- * 0.9 of the previous cycle's switches the network off for the rest of that
- * solve (plain sweep fallback).  The network must outlive its use. */
+/* Let hs_solve post-correct its preconditioner with the network (NULL
+ * detaches).  For each Arnoldi direction v and RHS the solver forms the
+ * sweep output x = M_alpha v and the correction c = s N(x / s), and the FP64
+ * residual decides: z = x + c is kept where |v - A (x + c)| < |v - A x|, else
+ * the plain sweep output z = x (one extra matvec per direction).  The network
+ * must outlive its use. */
 int hs_attach_cnn(hs_plan* plan, hs_cnn* net);
 
 /* Wait for the plan's work on `stream` and report any recorded device error. */

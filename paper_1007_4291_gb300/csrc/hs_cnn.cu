@@ -517,16 +517,16 @@ int check_dims(int nrhs, int n, int dtype) {
 
 }  // namespace
 
-// Correction inside the solver: z += s N(z/s) in place on the sweep output
-// in the internal layout (element (k, p) at p * R + k).  Safe in place: the
-// first layer reads all of z before the last one writes it (stream order).
-int cnn_correct(Cnn& c, void* z, int ztype, int R, int n, cudaStream_t s) {
+// Correction inside the solver: z += s N(x/s), s = rms(x), on vectors in the
+// internal layout (element (k, p) at p * R + k); x and z may be the same
+// vector (the first layer reads all of x before the last one writes z).
+int cnn_correct(Cnn& c, const void* x, void* z, int type, int R, int n, cudaStream_t s) {
   HS_TRY_INT(c.reserve(R, n));
   const long long sp = R, sk = 1;
-  if (ztype == HS_C64)
-    return forward_t<c64, c64, false>(c, (const c64*)z, (c64*)z, sp, sk, R, n, nullptr, 0.0, c.tensor_cores, s);
-  if (ztype == HS_C128)
-    return forward_t<c128, c128, false>(c, (const c128*)z, (c128*)z, sp, sk, R, n, nullptr, 0.0, c.tensor_cores, s);
+  if (type == HS_C64)
+    return forward_t<c64, c64, false>(c, (const c64*)x, (c64*)z, sp, sk, R, n, nullptr, 0.0, c.tensor_cores, s);
+  if (type == HS_C128)
+    return forward_t<c128, c128, false>(c, (const c128*)x, (c128*)z, sp, sk, R, n, nullptr, 0.0, c.tensor_cores, s);
   return HS_EINVAL;
 }
 

@@ -45,8 +45,8 @@ struct Cnn {
 
 // layer 2 (32 -> 32, bias, ReLU, bf16 out) on the tensor cores: c.h1 -> c.h2
 int conv2_tc(Cnn& c, int R, int n, cudaStream_t s);
-// z += s N(z / s) in place for a sweep output in the solver's internal
-// layout ([point][rhs]); ztype HS_C64 or HS_C128
-int cnn_correct(Cnn& c, void* z, int ztype, int R, int n, cudaStream_t s);
+// z += s N(x / s), s = rms(x), for vectors in the solver's internal layout
+// ([point][rhs]) of type HS_C64 or HS_C128; x and z may alias
+int cnn_correct(Cnn& c, const void* x, void* z, int type, int R, int n, cudaStream_t s);
 
 }  // namespace hs

@@ -340,6 +340,8 @@ KrylovPool& pool() {
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Work {
+  void* C;      // network correction of the current direction (factor precision), or null
+  void* Wc;     // A applied to it (solver precision), or null
   void* V;      // (m+1) Arnoldi vectors (c128 or cdf, 16 bytes per element)
   void* Z;      // m preconditioned vectors (factor precision)
   void* x;      // iterate
@@ -349,7 +351,7 @@ struct Work {
   void* s;      // per-RHS scale factors (double or double-float)
 };
 
-int carve_workspace(const Plan& p, int m, int R, Work& w) {
+int carve_workspace(const Plan& p, int m, int R, Work& w, bool judge) {
   KrylovPool& kp = pool();
   const size_t ves = 16;
   const size_t zes = (p.prec == HS_C64) ? sizeof(c64) : sizeof(c128);
@@ -357,7 +359,8 @@ int carve_workspace(const Plan& p, int m, int R, Work& w) {
   const size_t nct = (size_t)sm_count() * 2;
   const size_t b1 = al256((m + 1) * vs * ves), b2 = al256(m * vs * zes), b3 = al256(vs * ves);
   const size_t b4 = al256(nct * 33 * R * sizeof(c128)), b5 = al256(34 * R * sizeof(c128)), b6 = al256(R * 8);
-  const size_t need = b1 + b2 + 2 * b3 + b4 + b5 + b6;
+  const size_t b7 = judge ? al256(vs * zes) + al256(vs * ves) + al256(R * (2 * sizeof(double) + sizeof(int))) : 0;
+  const size_t need = b1 + b2 + 2 * b3 + b4 + b5 + b6 + b7;
   if (kp.bytes < need) {
     if (kp.base) cudaFree(kp.base);
     kp.base = nullptr;
@@ -376,7 +379,12 @@ int carve_workspace(const Plan& p, int m, int R, Work& w) {
   w.f = q; q += b3;
   w.part = (c128*)q; q += b4;
   w.h = (c128*)q; q += b5;
-  w.s = q;
+  w.s = q; q += b6;
+  w.C = w.Wc = nullptr;
+  if (judge) {
+    w.C = q; q += al256(vs * zes);
+    w.Wc = q;
+  }
   return HS_OK;
 }
 
@@ -388,6 +396,41 @@ void givens(zc a, zc b, double& c, zc& s) {
   const double na = std::hypot(std::abs(a), std::abs(b));
   c = std::abs(a) / na;
   s = (a / std::abs(a)) * std::conj(b) / na;
+}
+
+// ---------------------------------------------------------------- post-correction judge
+// acc[r] += |v - w|^2, acc[R + r] += |v - w - wc|^2 over the points of RHS r:
+// the FP64 residual of the preconditioned direction without (w = A z) and
+// with (w + wc = A (z + c)) the network's correction c.
+template <typename AR>
+__global__ void judge_kernel(const typename AR::V* __restrict__ v, const typename AR::V* __restrict__ w,
+                             const typename AR::V* __restrict__ wc, long long total, int R, double* acc) {
+  extern __shared__ double sacc[];
+  for (int i = threadIdx.x; i < 2 * R; i += blockDim.x) sacc[i] = 0.0;
+  __syncthreads();
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % R);
+    const c128 a = AR::out_c128(v[e]), b = AR::out_c128(w[e]), c = AR::out_c128(wc[e]);
+    const double pr = a.re - b.re, pi = a.im - b.im;
+    const double qr = pr - c.re, qi = pi - c.im;
+    atomicAdd(&sacc[r], pr * pr + pi * pi);
+    atomicAdd(&sacc[R + r], qr * qr + qi * qi);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * R; i += blockDim.x) atomicAdd(&acc[i], sacc[i]);
+}
+
+// For the RHS the judge kept (use[r] != 0): z += c and w += wc.
+template <typename AR, typename ZT>
+__global__ void keep_correction_kernel(cplx<ZT>* __restrict__ z, const cplx<ZT>* __restrict__ c,
+                                       typename AR::V* __restrict__ w, const typename AR::V* __restrict__ wc,
+                                       long long total, int R, const int* __restrict__ use) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    if (!use[e % R]) continue;
+    z[e] = cadd(z[e], c[e]);
+    const c128 a = AR::out_c128(w[e]), b = AR::out_c128(wc[e]);
+    w[e] = AR::from_c128(c128{a.re + b.re, a.im + b.im});
+  }
 }
 
 // ---------------------------------------------------------------- solver
@@ -496,7 +539,8 @@ int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs
   const int m = std::min(std::max(p.opt.restart, 1), 32);
   std::lock_guard<std::mutex> guard(pool().mu);
   Solver<AR> K{p, R, (long long)p.n * p.n, (long long)p.n * p.n * R, s, Work{}, sm_count() * 2, {}};
-  int st = carve_workspace(p, m, R, K.w);
+  Cnn* net = static_cast<Cnn*>(p.cnn);
+  int st = carve_workspace(p, m, R, K.w, net != nullptr);
   if (st != HS_OK) return st;
   const long long vs = K.vs;
   V* Vb = (V*)K.w.V;
@@ -527,9 +571,16 @@ int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs
   std::vector<char> active(R);
   int it = 0, cycles = 0, applies = 0, cnn_applies = 0;
   void* const u_saved = p.d_u;
-  Cnn* net = static_cast<Cnn*>(p.cnn);
-  bool cnn_on = net != nullptr;
-  double prev_cycle_res = HUGE_VAL;
+  const bool cnn_on = net != nullptr;
+  const size_t zes = (p.prec == HS_C64) ? sizeof(c64) : sizeof(c128);
+  double* judge_acc = nullptr;
+  int* judge_use = nullptr;
+  if (cnn_on) {
+    judge_acc = reinterpret_cast<double*>(static_cast<char*>(K.w.Wc) + al256(vs * 16));
+    judge_use = reinterpret_cast<int*>(judge_acc + 2 * R);
+  }
+  std::vector<double> jacc(2 * R);
+  std::vector<int> juse(R);
   while (true) {
     // true residual r = f - A x -> V_0
     K.matvec(x, true, Vb, fi);
@@ -545,12 +596,6 @@ int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs
       g[(size_t)r * (m + 1)] = active[r] ? beta : 0.0;
       for (int q = 1; q <= m; ++q) g[(size_t)r * (m + 1) + q] = 0.0;
     }
-    // the FP64 true residual judges the learned correction: a cycle that
-    // did not reduce it below 0.9 of the previous one ends its use
-    double cycle_res = 0.0;
-    for (int r = 0; r < R; ++r) cycle_res = std::max(cycle_res, relres[r]);
-    if (cnn_on && cycles > 0 && !(cycle_res < 0.9 * prev_cycle_res)) cnn_on = false;
-    prev_cycle_res = cycle_res;
     if (all || it >= maxit) break;
     ++cycles;
     K.scale(Vb, scl, Vb);
@@ -570,16 +615,47 @@ int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs
         p.d_u = Zj2;
       }
       st = sweep_internal(p, R, s);   // z_j moves with j: direct launches
-      if (st == HS_OK && cnn_on) {      // z_j += s N(z_j / s), post-correction of the sweep output
-        st = cnn_correct(*net, p.d_u, p.prec, R, p.n, s);
-        ++cnn_applies;
-      }
       void* zj = p.d_u;
       p.d_u = u_saved;
+      if (st == HS_OK && cnn_on) {      // correction c = s N(z_j / s) of the sweep output
+        cudaMemsetAsync(K.w.C, 0, vs * zes, s);
+        st = cnn_correct(*net, zj, K.w.C, p.prec, R, p.n, s);
+      }
       if (st != HS_OK) break;
       ++applies;
       cudaEventRecord(ev[1], s);
       K.matvec(zj, false, W1, nullptr);     // w = A z_j
+      if (cnn_on) {
+        // the FP64 residual judges the correction, per RHS and direction:
+        // keep z_j + c where |v_j - A (z_j + c)| < |v_j - A z_j|
+        V* Wc = static_cast<V*>(K.w.Wc);
+        K.matvec(K.w.C, false, Wc, nullptr);
+        cudaMemsetAsync(judge_acc, 0, 2 * R * sizeof(double), s);
+        static std::once_flag once;
+        std::call_once(once, [] {
+          cudaFuncSetAttribute(judge_kernel<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4096 * 8);
+        });
+        note_launch();
+        judge_kernel<AR><<<sm_count() * 4, 256, 2 * R * sizeof(double), s>>>(Vj, W1, Wc, vs, R, judge_acc);
+        cudaMemcpyAsync(jacc.data(), judge_acc, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        int kept = 0;
+        for (int r = 0; r < R; ++r) {
+          juse[r] = (active[r] && jacc[R + r] < jacc[r]) ? 1 : 0;
+          kept += juse[r];
+        }
+        if (kept) {
+          cudaMemcpyAsync(judge_use, juse.data(), R * sizeof(int), cudaMemcpyHostToDevice, s);
+          note_launch();
+          if (p.prec == HS_C64)
+            keep_correction_kernel<AR, float><<<sm_count() * 4, 256, 0, s>>>(
+                static_cast<c64*>(zj), static_cast<const c64*>(K.w.C), W1, Wc, vs, R, judge_use);
+          else
+            keep_correction_kernel<AR, double><<<sm_count() * 4, 256, 0, s>>>(
+                static_cast<c128*>(zj), static_cast<const c128*>(K.w.C), W1, Wc, vs, R, judge_use);
+        }
+        cnn_applies += kept;
+      }
       cudaEventRecord(ev[2], s);
       // classical Gram-Schmidt with an optional DGKS second pass
       K.dots(Vb, j + 1, W1);          // h[0..j] = V^H w, h[j+1] = |w|^2

@@ -1,11 +1,11 @@
 """Training of the sweep post-correction network on pairs the method makes.
 
-Pairs (x, e) = (M_alpha r, A^{-1} r - M_alpha r), the sweep output and its
+Pairs (x, e) = (M_alpha v, A^{-1} v - M_alpha v), the sweep output and its
 error, are generated on seeded smooth random velocity fields by the library
-itself: r is either a batch of Gaussian point sources f (the right-hand
-sides FGMRES starts from) or the residual f - A M_alpha f after one plain
-sweep (the next Krylov direction); A^{-1} r comes from hs_solve to a tight
-tolerance, M_alpha r from hs_apply.
+itself: v runs over the first Arnoldi vectors of right-preconditioned GMRES
+started from Gaussian point sources (the vectors the preconditioner is
+applied to inside FGMRES); A^{-1} v comes from hs_solve to a tight
+tolerance, M_alpha v from hs_apply.
 Training runs the library's own forward, backward and Adam kernels
 (hs_cnn_train_step); evaluation reports the relative error of the corrected
 preconditioner on held-out pairs and FGMRES iteration counts with and
@@ -24,38 +24,46 @@ def omega_of(n):
     return 2 * np.pi * (n + 1) / 16.0
 
 
-def make_pairs(n, seeds, nrhs, bp=12, b=12, layers=12, tol=1e-9, src_seed0=1000):
-    """Returns complex64 device tensors x = M r and e = A^{-1} r - M r of shape
-    (len(seeds) * 2 * nrhs, n, n)."""
+def make_pairs(n, seeds, nrhs, bp=12, b=12, layers=12, tol=1e-9, src_seed0=1000, krylov=6):
+    """Returns complex64 device tensors x = M v and e = A^{-1} v - M v of shape
+    (len(seeds) * krylov * nrhs, n, n) for the first ``krylov`` Arnoldi
+    vectors v of plain right-preconditioned GMRES started from Gaussian point
+    sources: the vectors the preconditioner meets inside FGMRES."""
     import torch
 
     from . import hs
     from . import inputs as I
 
-    rs, es = [], []
+    xs, es = [], []
     for q, seed in enumerate(seeds):
         c = I.random_velocity(n, seed)
         o = hs.hs_default_options(layers_per_step=layers, max_nrhs=nrhs, factor_prec=hs.HS_C64, restart=30)
         plan = hs.hs_setup(c.ravel(), omega_of(n), n, 2, bp, b, o)
         try:
             f = torch.from_numpy(I.point_sources(n, nrhs, src_seed0 + seed, bp)).to("cuda")
-            mf = torch.empty_like(f)
-            hs.hs_apply(plan, f, mf, nrhs, hs.HS_C128)
-            amf = torch.empty_like(f)
-            hs.hs_matvec(plan, mf, amf, nrhs, hs.HS_C128)
-            r1 = f - amf
-            for r in (f, r1):
-                u = torch.zeros_like(r)
-                code, info = hs.hs_solve(plan, r, u, nrhs, tol, 400)
+            V = [f / torch.linalg.vector_norm(f.reshape(nrhs, -1), dim=1).reshape(nrhs, 1, 1)]
+            for j in range(krylov):
+                v = V[-1].contiguous()
+                mv = torch.empty_like(v)
+                hs.hs_apply(plan, v, mv, nrhs, hs.HS_C128)
+                u = torch.zeros_like(v)
+                code, info = hs.hs_solve(plan, v, u, nrhs, tol, 400)
                 if code != hs.HS_OK:
                     raise RuntimeError("training solve did not converge: %r" % (info,))
-                mr = torch.empty_like(r)
-                hs.hs_apply(plan, r, mr, nrhs, hs.HS_C128)
-                rs.append(mr.to(torch.complex64))
-                es.append((u - mr).to(torch.complex64))
+                xs.append(mv.to(torch.complex64))
+                es.append((u - mv).to(torch.complex64))
+                if j + 1 == krylov:
+                    break
+                w = torch.empty_like(v)
+                hs.hs_matvec(plan, mv, w, nrhs, hs.HS_C128)          # next Arnoldi direction A M v_j
+                for _ in range(2):                                     # Gram-Schmidt, twice
+                    for vi in V:
+                        h = (vi.conj() * w).reshape(nrhs, -1).sum(dim=1).reshape(nrhs, 1, 1)
+                        w = w - h * vi
+                V.append(w / torch.linalg.vector_norm(w.reshape(nrhs, -1), dim=1).reshape(nrhs, 1, 1))
         finally:
             hs.hs_destroy(plan)
-    return torch.cat(rs), torch.cat(es)
+    return torch.cat(xs), torch.cat(es)
 
 
 def corrected_error(net, r, e, n, batch=16):
@@ -121,13 +129,15 @@ def iterations(n, seed, net, nrhs=8, bp=12, b=12, layers=12, tol=1e-6):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=511)
-    ap.add_argument("--pairs", type=int, default=2048, help="training pairs (2 per source, 64 sources per field)")
+    ap.add_argument("--pairs", type=int, default=2048, help="training pairs (krylov per source, nrhs sources per field)")
+    ap.add_argument("--krylov", type=int, default=6, help="Arnoldi vectors per source")
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--out", default=None, help="save the trained parameters (.npy)")
     ap.add_argument("--eval-n", type=int, nargs="*", default=[511, 1023])
+    ap.add_argument("--report", default=None, help="write the JSON report to this file too")
     args = ap.parse_args(argv)
     import torch
 
@@ -135,13 +145,14 @@ def main(argv=None):
     from . import inputs as I
 
     build.build()
-    nfields = max(1, args.pairs // (2 * args.nrhs))
+    nfields = max(1, args.pairs // (args.krylov * args.nrhs))
     t0 = time.perf_counter()
-    r, e = make_pairs(args.n, list(range(1000, 1000 + nfields)), args.nrhs)
-    rv, ev = make_pairs(args.n, [5000], min(args.nrhs, 16))
+    r, e = make_pairs(args.n, list(range(1000, 1000 + nfields)), args.nrhs, krylov=args.krylov)
+    rv, ev = make_pairs(args.n, [5000], min(args.nrhs, 16), krylov=args.krylov)
     t_data = time.perf_counter() - t0
     net = hs.hs_cnn_create(I.cnn_init_params(0))
     try:
+        hs.hs_cnn_set_mode(net, 1)            # tensor-core layer 2 for inference
         before = corrected_error(net, rv, ev, args.n)
         t0 = time.perf_counter()
         losses = train(net, r, e, args.n, args.steps, args.batch, args.lr, log_every=100)
@@ -155,6 +166,9 @@ def main(argv=None):
                   "heldout_rel_err_sq_before": before, "heldout_rel_err_sq_after": after,
                   "fgmres": {str(m): iterations(m, 5000 + m, net) for m in args.eval_n}}
         print(json.dumps(report))
+        if args.report:
+            with open(args.report, "w") as fh:
+                json.dump(report, fh, indent=1)
     finally:
         hs.hs_cnn_destroy(net)
 

@@ -127,8 +127,9 @@ def test_training_learns_a_teacher_network():
 
 
 def test_solve_with_attached_network_reaches_tolerance():
-    """FGMRES with z = M v + s N(v/s): the FP64 true residual still decides;
-    an untrained (harmful) network is switched off and the solve converges."""
+    """FGMRES with the post-correction judged per direction by the FP64
+    residual: with an untrained network the solve still converges to the
+    tolerance (the judge falls back to the plain sweep output)."""
     from oracle import helmholtz2d as H
     n, bp = 63, 8
     c = I.random_velocity(n, 2)
@@ -144,7 +145,7 @@ def test_solve_with_attached_network_reaches_tolerance():
         ug = torch.zeros_like(fg)
         code, info = hs.hs_solve(plan, fg, ug, R, 1e-6, 300)
         assert code == hs.HS_OK, info
-        assert info["cnn_applies"] > 0
+        assert 0 <= info["cnn_applies"] <= info["iterations"] * R
         A0 = H.helmholtz_matrix(c, omega, bp, 20.0, 0.0)
         u = ug.cpu().numpy()
         for k in range(R):
@@ -160,8 +161,8 @@ def test_trained_network_reduces_heldout_sweep_error():
     on a held-out field is below the plain sweep's (which scores 1)."""
     from paper_1007_4291_gb300 import train_cnn as T
     n = 63
-    r, e = T.make_pairs(n, [1000, 1001, 1002], 8, bp=8, b=8, layers=4)
-    rv, ev = T.make_pairs(n, [5000], 8, bp=8, b=8, layers=4)
+    r, e = T.make_pairs(n, [1000, 1001, 1002], 8, bp=8, b=8, layers=4, krylov=4)
+    rv, ev = T.make_pairs(n, [5000], 8, bp=8, b=8, layers=4, krylov=4)
     net = hs.hs_cnn_create(I.cnn_init_params(0))
     try:
         before = T.corrected_error(net, rv, ev, n)
@@ -169,5 +170,8 @@ def test_trained_network_reduces_heldout_sweep_error():
         after = T.corrected_error(net, rv, ev, n)
         print("held-out relative squared error: plain 1.0, init %.4f, trained %.4f" % (before, after))
         assert after < 1.0 and after < before
+        its = T.iterations(n, 5001, net, nrhs=4, bp=8, b=8, layers=4)
+        print("FGMRES iterations to 1e-6 at n = %d: %r" % (n, its))
+        assert its["cnn"]["status"] == hs.HS_OK and its["cnn"]["max_relres"] <= 1e-6
     finally:
         hs.hs_cnn_destroy(net)
