@@ -109,6 +109,8 @@ struct Plan {
   long long uid = 0;        // process-unique id (keys of cached CUDA graphs)
   void* graphs = nullptr;   // cached executable graphs of this plan's sweep (hs_sweep.cu)
   void* cnn = nullptr;      // attached post-correction network (hs_cnn.cuh), not owned
+  void* p3 = nullptr;       // 3D plan data (hs3d.cuh) when dim == 3
+  long long npts() const { return dim == 3 ? (long long)n * n * n : (long long)n * n; }
 };
 
 // ---------------------------------------------------------------- helpers
@@ -119,6 +121,8 @@ inline void note_launch(long long k = 1) { g_launches.fetch_add(k, std::memory_o
 #define HS_CUDA_TRY(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) return hs::cuda_status(_e); } while (0)
 
 int padded_width(int w);   // 8, 12, 16, 24, 32 or -1
+// two-front block partition of Sec. 2.3 (rows in 2D, x3 layers in 3D) into p.blocks/stages/middle
+void build_blocks(Plan& p);
 
 // Capture the launches body(stream) makes on `cap` into an executable graph.
 // Kernels counted by note_launch during the capture did not run: they are

@@ -355,7 +355,7 @@ int carve_workspace(const Plan& p, int m, int R, Work& w, bool judge) {
   KrylovPool& kp = pool();
   const size_t ves = 16;
   const size_t zes = (p.prec == HS_C64) ? sizeof(c64) : sizeof(c128);
-  const size_t npts = (size_t)p.n * p.n, vs = npts * R;
+  const size_t npts = (size_t)p.npts(), vs = npts * R;
   const size_t nct = (size_t)sm_count() * 2;
   const size_t b1 = al256((m + 1) * vs * ves), b2 = al256(m * vs * zes), b3 = al256(vs * ves);
   const size_t b4 = al256(nct * 33 * R * sizeof(c128)), b5 = al256(34 * R * sizeof(c128)), b6 = al256(R * 8);
@@ -503,8 +503,7 @@ struct Solver {
   // (solver_vec) or a preconditioned vector in the factor precision.
   void matvec(const void* x, bool solver_vec, V* y, const V* f) {
     if constexpr (std::is_same<AR, F64>::value) {
-      matvec_internal_f64(p, x, false, y, f, R, s);
-      (void)solver_vec;
+      matvec_internal_f64(p, x, !solver_vec && p.prec == HS_C64, y, f, R, s);
     } else {
       DfTabs t{(const cdf*)p.k_inv_s1, (const cdf*)p.k_a1, (const cdf*)p.k_inv_s2, (const cdf*)p.k_a2,
                (const df*)p.k_m0, p.d_pml1, p.d_pml2, (float)((double)(p.n + 1) * (p.n + 1))};
@@ -538,8 +537,8 @@ int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs
   const int R = nrhs;
   const int m = std::min(std::max(p.opt.restart, 1), 32);
   std::lock_guard<std::mutex> guard(pool().mu);
-  Solver<AR> K{p, R, (long long)p.n * p.n, (long long)p.n * p.n * R, s, Work{}, sm_count() * 2, {}};
-  Cnn* net = static_cast<Cnn*>(p.cnn);
+  Solver<AR> K{p, R, p.npts(), p.npts() * R, s, Work{}, sm_count() * 2, {}};
+  Cnn* net = p.dim == 2 ? static_cast<Cnn*>(p.cnn) : nullptr;
   int st = carve_workspace(p, m, R, K.w, net != nullptr);
   if (st != HS_OK) return st;
   const long long vs = K.vs;
@@ -766,12 +765,14 @@ extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double 
   Plan& p = *reinterpret_cast<Plan*>(plan);
   if (nrhs < 1 || nrhs > p.max_nrhs) return HS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  return (p.prec == HS_C64) ? solve_t<DF64>(p, f, u, nrhs, tol, maxit, info, s)
-                            : solve_t<F64>(p, f, u, nrhs, tol, maxit, info, s);
+  // 3D plans keep the Krylov vectors in FP64 (the double-float kernels are 2D)
+  return (p.prec == HS_C64 && p.dim == 2) ? solve_t<DF64>(p, f, u, nrhs, tol, maxit, info, s)
+                                          : solve_t<F64>(p, f, u, nrhs, tol, maxit, info, s);
 }
 
 extern "C" int hs_attach_cnn(hs_plan* plan, hs_cnn* net) {
   if (!plan) return HS_EINVAL;
+  if (reinterpret_cast<Plan*>(plan)->dim != 2) return HS_EUNSUPPORTED;
   reinterpret_cast<Plan*>(plan)->cnn = net;
   return HS_OK;
 }

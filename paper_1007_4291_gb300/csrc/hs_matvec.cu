@@ -8,6 +8,7 @@
 // One thread per (point, RHS) element; both vector layouts are supported:
 // RHS-outer (the ABI layout, x1 fastest) and RHS-inner (the solver's layout).
 #include "hs_internal.cuh"
+#include "hs3d.cuh"
 
 namespace hs {
 namespace {
@@ -104,6 +105,7 @@ int matvec_abi(Plan& p, const void* x, void* y, int nrhs, int dtype, cudaStream_
 }
 
 int matvec_internal_f64(Plan& p, const void* x, bool x_is_c64, c128* y, const c128* f, int R, cudaStream_t s) {
+  if (p.dim == 3) return matvec3_internal_f64(p, x, x_is_c64, y, f, R, s);
   const long long total = (long long)p.n * p.n * R;
   const int g = grid_for(total);
   note_launch();
@@ -126,5 +128,6 @@ extern "C" int hs_matvec(hs_plan* plan, const void* x, void* y, int nrhs, int dt
   if (!plan || !x || !y || x == y) return HS_EINVAL;
   Plan& p = *reinterpret_cast<Plan*>(plan);
   if (nrhs < 1 || (dtype != HS_C64 && dtype != HS_C128)) return HS_EINVAL;
+  if (p.dim == 3) return matvec3_abi(p, x, y, nrhs, dtype, (cudaStream_t)stream);
   return matvec_abi(p, x, y, nrhs, dtype, (cudaStream_t)stream);
 }

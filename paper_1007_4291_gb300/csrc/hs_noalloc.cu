@@ -56,6 +56,7 @@ extern "C" int hs_apply_noalloc(hs_plan* plan, const void* r, void* z, int nrhs,
   if (!plan || !r || !z) return HS_EINVAL;
   Plan& p = *reinterpret_cast<Plan*>(plan);
   if (nrhs < 1 || (dtype != HS_C64 && dtype != HS_C128)) return HS_EINVAL;
+  if (p.dim != 2) return HS_EUNSUPPORTED;
   int Wmax = 0;
   for (const auto& d : p.blocks) Wmax = d.W > Wmax ? d.W : Wmax;
   const size_t es = (p.prec == HS_C64) ? sizeof(c64) : sizeof(c128);

@@ -10,6 +10,7 @@
 #include <atomic>
 #include "hs_internal.cuh"
 #include "hs_device.cuh"
+#include "hs3d.cuh"
 
 namespace hs {
 
@@ -61,6 +62,8 @@ template <typename T> int dalloc(Plan& p, T** ptr, size_t count) {
 }
 #define HS_TRY(expr) do { int _s = (expr); if (_s != HS_OK) return _s; } while (0)
 
+}  // namespace
+
 // Two-front partition: F, d-row lower blocks (last one takes the remainder),
 // the middle layer (n+1)/2, and the mirrored upper front ending at E.
 void build_blocks(Plan& p) {
@@ -99,7 +102,6 @@ void build_blocks(Plan& p) {
   }
 }
 
-}  // namespace
 }  // namespace hs
 
 using namespace hs;
@@ -149,6 +151,7 @@ extern "C" int hs_destroy(hs_plan* plan) {
   cudaDeviceSynchronize();
   forget_batch_graphs(p->uid);
   release_sweep_graphs(*p);
+  release_plan3(*p);
   free_plan_memory(p);
   delete p;
   return HS_OK;
@@ -179,6 +182,62 @@ extern "C" int hs_sync(hs_plan* plan, void* stream) {
   return hs_last_device_status(plan);
 }
 
+// 3D plan: validation, the 1D stretch tables (all axes share the boundary
+// profile), omega^2/c^2 and 1/c^2 per point, the block partition in x3
+// layers, and the slab-solver workspace (hs3d.cu).
+static int prepare_plan3d(const double* c, double omega, int n, int pml_width, int moving_pml_width,
+                          const hs_options* opt_in, Plan** out) {
+  if (n < 3 || n % 2 != 1 || pml_width < 1 || 2 * pml_width + 1 > n) return HS_EINVAL;
+  if (moving_pml_width < 1 || moving_pml_width > pml_width + 1) return HS_EINVAL;
+  if (n > 255) return HS_EUNSUPPORTED;
+  hs_options opt;
+  hs_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (!(opt.alpha >= 0.0) || !(opt.pml_C >= 0.0) || opt.layers_per_step < 1 || opt.max_nrhs < 1 ||
+      opt.max_nrhs > 4096 || opt.restart < 1)
+    return HS_EINVAL;
+  if (opt.factor_prec != HS_C64 && opt.factor_prec != HS_C128) return HS_EINVAL;
+  const size_t N3 = (size_t)n * n * n;
+  for (size_t k = 0; k < N3; ++k)
+    if (!(c[k] > 0.0) || !std::isfinite(c[k])) return HS_EINVAL;
+  Plan* p = new Plan();
+  p->n = n; p->dim = 3; p->bp = pml_width; p->b = moving_pml_width; p->dL = opt.layers_per_step;
+  p->omega = omega; p->alpha = opt.alpha; p->C = opt.pml_C; p->h = 1.0 / (n + 1);
+  p->prec = opt.factor_prec; p->max_nrhs = opt.max_nrhs; p->opt = opt;
+  p->opt.tune_cache = nullptr;
+  build_blocks(*p);
+  int st = HS_OK;
+  auto fail = [&](int code) { release_plan3(*p); free_plan_memory(p); delete p; return code; };
+  const double h = p->h, eta = p->bp * h, C = p->C;
+  std::vector<c128> inv_s(n + 2), a_half(n + 1);
+  std::vector<unsigned char> pml(n + 2, 0);
+  for (int k = 0; k <= n + 1; ++k) inv_s[k] = to_c(inv_stretch(sigma_boundary(k * h, eta, C), omega));
+  for (int k = 0; k <= n; ++k) a_half[k] = to_c(stretch(sigma_boundary((k + 0.5) * h, eta, C), omega) / (h * h));
+  std::vector<double> m0(N3), ci2(N3);
+  for (size_t k = 0; k < N3; ++k) {
+    ci2[k] = 1.0 / (c[k] * c[k]);
+    m0[k] = omega * omega * ci2[k];
+  }
+  const size_t es = (p->prec == HS_C64) ? sizeof(c64) : sizeof(c128);
+  if ((st = dalloc(*p, &p->d_inv_s1, n + 2)) || (st = dalloc(*p, &p->d_a1, n + 1)) ||
+      (st = dalloc(*p, &p->d_m0, N3)) || (st = dalloc(*p, &p->d_cinv2, N3)) ||
+      (st = dalloc(*p, &p->d_blocks, p->blocks.size())) || (st = dalloc(*p, &p->d_status, 4)) ||
+      (st = dalloc(*p, (char**)&p->d_u, N3 * (size_t)p->max_nrhs * es)))
+    return fail(st);
+  cudaMemcpy(p->d_inv_s1, inv_s.data(), (n + 2) * sizeof(c128), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_a1, a_half.data(), (n + 1) * sizeof(c128), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_m0, m0.data(), N3 * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_cinv2, ci2.data(), N3 * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemset(p->d_status, 0, 4 * sizeof(int));
+  if ((st = prepare_plan3(*p)) != HS_OK) return fail(st);
+  cudaMemcpy(p->d_blocks, p->blocks.data(), p->blocks.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice);
+  if (cudaGetLastError() != cudaSuccess) return fail(HS_ECUDA);
+  static std::atomic<long long> next_uid3{1LL << 40};
+  p->uid = next_uid3.fetch_add(1);
+  *out = p;
+  return HS_OK;
+}
+
 // Validate the arguments, build the host tables of one problem and allocate
 // and fill its device memory (no kernel launches).  On failure nothing is
 // left allocated.
@@ -186,7 +245,8 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
                         const hs_options* opt_in, Plan** out) {
   *out = nullptr;
   if (!c || !(omega > 0.0) || !std::isfinite(omega)) return HS_EINVAL;
-  if (dim != 2) return (dim == 3) ? HS_EUNSUPPORTED : HS_EINVAL;
+  if (dim != 2 && dim != 3) return HS_EINVAL;
+  if (dim == 3) return prepare_plan3d(c, omega, n, pml_width, moving_pml_width, opt_in, out);
   if (n < 3 || n % 2 != 1 || pml_width < 1 || 2 * pml_width + 1 > n) return HS_EINVAL;
   if (moving_pml_width < 1 || moving_pml_width > pml_width + 1) return HS_EINVAL;
   hs_options opt;
@@ -345,13 +405,23 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
 
 static void drop_plan(Plan* p) {
   release_sweep_graphs(*p);
+  release_plan3(*p);
   free_plan_memory(p);
   delete p;
 }
 
 // Factor the prepared plans together and check their status words.
 static int factor_plans(std::vector<Plan*>& ps, cudaStream_t s) {
-  int st = launch_setup(ps, s);
+  std::vector<Plan*> p2;
+  for (Plan* p : ps) {
+    if (p->dim == 3) {
+      int st3 = setup3(*p, s);
+      if (st3 != HS_OK) return st3;
+    } else {
+      p2.push_back(p);
+    }
+  }
+  int st = launch_setup(p2, s);
   if (st != HS_OK) return st;
   for (Plan* p : ps) {
     int dst[3];

@@ -24,6 +24,7 @@
 #include <algorithm>
 #include "hs_internal.cuh"
 #include "hs_device.cuh"
+#include "hs3d.cuh"
 
 namespace hs {
 namespace {
@@ -930,6 +931,7 @@ struct SweepGraphs {
 }  // namespace
 
 int sweep_internal(Plan& p, int nrhs, cudaStream_t s, bool graph) {
+  if (p.dim == 3) return sweep3(p, nrhs, s);
   if (!graph) return sweep_launch(p, nrhs, s);
   if (!p.graphs) p.graphs = new SweepGraphs();
   SweepGraphs& gs = *static_cast<SweepGraphs*>(p.graphs);
@@ -987,7 +989,7 @@ extern "C" int hs_apply(hs_plan* plan, const void* r, void* z, int nrhs, int dty
   Plan& p = *reinterpret_cast<Plan*>(plan);
   if (nrhs < 1 || nrhs > p.max_nrhs || (dtype != HS_C64 && dtype != HS_C128)) return HS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  const int n2 = p.n * p.n;
+  const int n2 = (int)p.npts();
   int st = layout_to_internal(r, dtype, p.d_u, p.prec, n2, nrhs, s);
   if (st == HS_OK) st = sweep_internal(p, nrhs, s, p.opt.graphs != 0);
   if (st == HS_OK) st = layout_from_internal(p.d_u, p.prec, z, dtype, n2, nrhs, s);

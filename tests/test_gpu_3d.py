@@ -1,0 +1,116 @@
+"""GPU parity of the 3D path (7-point operator, slab sweep with the
+nested-dissection multifrontal solves) against the complex128 oracle.
+
+Tolerances as in 2D: FP64 matvec 1e-12, complex64 matvec 2e-5; sweep
+applications 1e-4 (complex64 factors) and 1e-10 (complex128 factors); solves
+must reach the requested residual under the oracle's FP64 operator.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import helmholtz3d as H3
+from paper_1007_4291_gb300 import build as B
+from paper_1007_4291_gb300 import hs
+from paper_1007_4291_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+C_PML = 20.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    B.build()
+    return hs.load()
+
+
+def relerr(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def plan3(c, omega, bp, b, dL, prec=hs.HS_C64, alpha=1.0, R=4):
+    n = c.shape[0]
+    o = hs.hs_default_options(alpha=alpha, pml_C=C_PML, layers_per_step=dL, factor_prec=prec, max_nrhs=R)
+    return hs.hs_setup(c.ravel(), omega, n, 3, bp, b, o)
+
+
+@pytest.mark.parametrize("dtype,tol", [(hs.HS_C128, 1e-12), (hs.HS_C64, 2e-5)])
+def test_matvec3_matches_oracle(dtype, tol):
+    n = 9
+    c = I.random_velocity(n, 1, dim=3)
+    omega, bp = 2 * np.pi * 1.5, 2
+    p = plan3(c, omega, bp, bp, 1)
+    try:
+        x = I.random_rhs(n, 2, 3, dim=3)
+        tdt = torch.complex64 if dtype == hs.HS_C64 else torch.complex128
+        xg = torch.from_numpy(x).to("cuda").to(tdt)
+        yg = torch.empty_like(xg)
+        hs.hs_matvec(p, xg, yg, 2, dtype)
+        y = yg.cpu().numpy().astype(np.complex128)
+        xin = xg.cpu().numpy().astype(np.complex128)
+        ref = H3.apply_stencil(H3.coefficients(c, omega, bp, C_PML, 0.0), xin)
+        assert relerr(y, ref) <= tol
+    finally:
+        hs.hs_destroy(p)
+
+
+CASES = [
+    # n, bp, b, dL, R
+    (11, 2, 2, 1, 2),
+    (13, 3, 3, 2, 3),      # remainder block, b = bp
+    (17, 4, 3, 1, 1),      # b < bp, deeper dissection tree
+    (9, 2, 3, 3, 2),       # d larger than a front: one block per front
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("prec", [hs.HS_C64, hs.HS_C128])
+def test_apply3_matches_oracle(case, prec):
+    n, bp, b, dL, R = case
+    c = I.random_velocity(n, 5, dim=3)
+    omega, alpha = 2 * np.pi * 1.5, 1.0
+    p = plan3(c, omega, bp, b, dL, prec=prec, alpha=alpha, R=R)
+    try:
+        r = I.random_rhs(n, R, 6, dim=3)
+        io = prec
+        tdt = torch.complex64 if io == hs.HS_C64 else torch.complex128
+        rg = torch.from_numpy(r).to("cuda").to(tdt)
+        zg = torch.empty_like(rg)
+        hs.hs_apply(p, rg, zg, R, io)
+        torch.cuda.synchronize()
+        assert hs.hs_last_device_status(p) == hs.HS_OK
+        z = zg.cpu().numpy().astype(np.complex128)
+        st = H3.setup(c, omega, bp, b, dL, alpha, C_PML)
+        ref = H3.apply(st, rg.cpu().numpy().astype(np.complex128))
+        tol = 1e-4 if prec == hs.HS_C64 else 1e-10
+        for k in range(R):
+            assert relerr(z[k], ref[k]) <= tol, (k, relerr(z[k], ref[k]))
+    finally:
+        hs.hs_destroy(p)
+
+
+@pytest.mark.parametrize("prec", [hs.HS_C64, hs.HS_C128])
+def test_solve3_reaches_tolerance_under_oracle_operator(prec):
+    n, bp, b = 15, 4, 4
+    c = I.random_velocity(n, 9, dim=3)
+    omega = 2 * np.pi * (n + 1) / 8.0
+    R = 2
+    p = plan3(c, omega, bp, b, 1, prec=prec, R=R)
+    try:
+        f = I.point_sources(n, R, 10, bp, dim=3)
+        fg = torch.from_numpy(f).to("cuda")
+        ug = torch.zeros_like(fg)
+        code, info = hs.hs_solve(p, fg, ug, R, 1e-6, 200)
+        assert code == hs.HS_OK, info
+        A0 = H3.helmholtz_matrix(c, omega, bp, C_PML, 0.0)
+        u = ug.cpu().numpy()
+        for k in range(R):
+            res = np.linalg.norm(f[k].ravel() - A0 @ u[k].ravel()) / np.linalg.norm(f[k].ravel())
+            assert res <= 1e-6
+        assert info["iterations"] <= 25
+    finally:
+        hs.hs_destroy(p)

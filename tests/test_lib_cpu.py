@@ -70,7 +70,12 @@ def test_setup_rejects_bad_velocity_and_options(lib):
     o.factor_prec = 32
     assert lib.hs_setup(c.ctypes.data, 10.0, n, 2, 3, 3, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EINVAL
     o = hs.hs_default_options()
-    assert lib.hs_setup(c.ctypes.data, 10.0, n, 3, 3, 3, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EUNSUPPORTED
+    assert lib.hs_setup(c.ctypes.data, 10.0, n, 4, 3, 3, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EINVAL
+    # 3D: sizes are checked before the n^3 velocities are read
+    assert lib.hs_setup(c.ctypes.data, 10.0, 257, 3, 3, 3, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EUNSUPPORTED
+    c3 = np.ones(7 ** 3)
+    c3[100] = 0.0
+    assert lib.hs_setup(c3.ctypes.data, 10.0, 7, 3, 2, 2, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EINVAL
     assert lib.hs_setup(None, 10.0, n, 2, 3, 3, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EINVAL
     assert lib.hs_apply(None, None, None, 1, 64, None) == hs.HS_EINVAL
     assert lib.hs_destroy(None) == hs.HS_OK
