@@ -60,6 +60,9 @@ typedef struct {
   int graphs;            /* 1: hs_apply replays the stage chain of the sweep as a CUDA graph
                             (captured on first use per nrhs); 0: direct launches.  hs_solve
                             sweeps a different Krylov vector at every step and launches directly. default 1 */
+  int frontal_gemm;      /* 3D setup, frontal Schur updates of complex64 factors: 0 CUDA-core FP32
+                            FMA, 1 TF32 tensor cores (one pass), 3 3xTF32 tensor cores (split
+                            operands, FP32-level accuracy).  Complex128 factors use FP64 FMA.   default 3 */
   const char* tune_cache;/* path of the chunk-length table written by hs_autotune; with chunk = 0,
                             hs_setup takes the chunk length from it when it holds the problem's
                             key.  NULL: not used.  The string must outlive the hs_setup call.    default NULL */
@@ -86,11 +89,14 @@ int hs_default_options(hs_options* opt);
 /*
  * hs_setup -- build the sweeping factorisation (Algorithm 3, Sec. 2.3).
  *
- * c        HOST pointer to n*n velocities c(ih, jh) (double, x1 fastest), c > 0.
+ * c        HOST pointer to n^dim velocities c (double, x1 fastest, then x2, x3), c > 0.
  * omega    angular frequency omega > 0 (Sec. 1).
  * n        grid points per axis; odd, so that the two fronts meet at the middle
  *          layer (n+1)/2 (Sec. 2.3).
- * dim      2 (3D plans are not built by this entry point: HS_EUNSUPPORTED).
+ * dim      2, or 3 for the 7-point operator of Sec. 4 (Eq. helmd3) on n^3 points with
+ *          the slab sweep of Algorithms 5 and 6 (two fronts in x3, d layers per step;
+ *          each slab solved by a nested-dissection multifrontal factorisation of
+ *          the (x1, x2) plane; n <= 255).
  * pml_width         b_p: boundary PML width in grid points, eta = b_p h (Eq. sigma).
  * moving_pml_width  b: moving PML width in grid points (Eq. helma), 1 <= b <= b_p + 1.
  * opt      NULL for defaults.

@@ -1,0 +1,193 @@
+// Frontal updates of the 3D multifrontal setup on the tensor cores: batched
+// complex GEMMs C = beta C + alpha A B (complex64) as real TF32 GEMMs with
+// FP32 accumulation in tensor memory.
+//
+// Complex product as one real product (the "4M" form): with A read as the
+// real M x 2K matrix of its interleaved (re, im) storage and
+//   Bt[2n + c][2k + d] = { Br, -Bi ; Bi, Br }[c][d]   (rows = output columns),
+// the interleaved complex result is A Bt^t.  Precision modes: one TF32 pass
+// (operands truncated to 10-bit mantissas), or the 3xTF32 split a = a_hi +
+// a_lo with a_hi b_hi + a_hi b_lo + a_lo b_hi, which restores FP32 accuracy.
+//
+// A CTA computes a 128 x 32 complex tile (MMA M = 128, N = 64 real columns)
+// and loops over K in chunks of 16 complex (32 real) values: its threads
+// write the A and Bt chunks to shared memory in the K-major non-swizzled
+// core-matrix layout ([k/4][row][4] floats), one thread issues the MMAs
+// (K = 8 each) and commits them, and every thread waits on the mbarrier
+// (bounded) before the chunk's buffers are reused.  The epilogue reads the
+// accumulator rows of each warp's TMEM lane quarter.
+#include <algorithm>
+#include "hs_internal.cuh"
+#include "hs_device.cuh"
+#include "hs_tc.cuh"
+#include "hs3d_tc.cuh"
+
+namespace hs {
+namespace {
+
+constexpr int TM = 128;        // tile rows (MMA M)
+constexpr int TNC = 32;        // tile columns, complex
+constexpr int TN = 2 * TNC;    // MMA N (real)
+constexpr int KC = 16;         // complex K per chunk
+constexpr int KR = 2 * KC;     // real K per chunk
+constexpr uint32_t A_BYTES = TM * KR * 4;   // 16 KB
+constexpr uint32_t B_BYTES = TN * KR * 4;   //  8 KB
+constexpr uint32_t A_LBO = TM * 16, B_LBO = TN * 16;
+constexpr uint32_t IDESC = tc_idesc(2u, TM, TN);    // TF32 A and B, FP32 accumulator
+// Requested shared memory: the two precision halves of A and B plus the
+// barrier; generous so that every address a descriptor forms stays inside.
+constexpr uint32_t SMEM_BYTES = 96 * 1024;
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+__device__ __forceinline__ void put(float* buf, int rows, int r, int k, float v) {
+  buf[((k >> 2) * rows + r) * 4 + (k & 3)] = v;
+}
+
+__global__ void __launch_bounds__(128, 1) zgemm_tf32_kernel(const TcGemmJob* jobs, const TcGemmTile* tiles, int split,
+                                                           int* status, long long spin) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  float* Ah = reinterpret_cast<float*>(sm);
+  float* Al = reinterpret_cast<float*>(sm + A_BYTES);
+  float* Bh = reinterpret_cast<float*>(sm + 2 * A_BYTES);
+  float* Bl = reinterpret_cast<float*>(sm + 2 * A_BYTES + B_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * A_BYTES + 2 * B_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const TcGemmTile tl = tiles[blockIdx.x];
+  const TcGemmJob jb = jobs[tl.job];
+  const c64* A = static_cast<const c64*>(jb.A);
+  const c64* B = static_cast<const c64*>(jb.B);
+  c64* Cm = static_cast<c64*>(jb.C);
+  const int m0 = tl.tm * TM, n0 = tl.tn * TNC;
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tc_alloc(tslot, TN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
+  uint32_t phase = 0;
+  bool ok = true;
+  const int nchunks = (jb.K + KC - 1) / KC;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int k0 = ch * KC;
+    // A chunk: row r = tid, 16 complex values
+    {
+      const int m = m0 + tid;
+#pragma unroll 4
+      for (int kk = 0; kk < KC; ++kk) {
+        const int k = k0 + kk;
+        c64 v{0.f, 0.f};
+        if (m < jb.M && k < jb.K) v = A[(long long)m * jb.lda + k];
+        const float hr = split ? tf32_hi(v.re) : v.re, hi_ = split ? tf32_hi(v.im) : v.im;
+        put(Ah, TM, tid, 2 * kk, hr);
+        put(Ah, TM, tid, 2 * kk + 1, hi_);
+        if (split) {
+          put(Al, TM, tid, 2 * kk, v.re - hr);
+          put(Al, TM, tid, 2 * kk + 1, v.im - hi_);
+        }
+      }
+    }
+    // Bt chunk: (k, n) pairs of the chunk, 4 per thread
+    for (int e = tid; e < KC * TNC; e += blockDim.x) {
+      const int kk = e / TNC, nn = e % TNC;
+      const int k = k0 + kk, n = n0 + nn;
+      c64 v{0.f, 0.f};
+      if (k < jb.K && n < jb.N) v = B[(long long)k * jb.ldb + n];
+      const float vals[4] = {v.re, -v.im, v.im, v.re};   // (c, d) = (0,0), (0,1), (1,0), (1,1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int row = 2 * nn + (q >> 1), col = 2 * kk + (q & 1);
+        const float x = vals[q];
+        const float h = split ? tf32_hi(x) : x;
+        put(Bh, TN, row, col, h);
+        if (split) put(Bl, TN, row, col, x - h);
+      }
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll 1
+      for (int kk = 0; kk < KR / 8; ++kk) {
+        const uint32_t ao = (uint32_t)(2 * kk) * A_LBO, bo = (uint32_t)(2 * kk) * B_LBO;
+        const uint32_t first = (ch == 0 && kk == 0) ? 0u : 1u;
+        tc_mma_tf32(tmem, tc_smem_desc(ah + ao, A_LBO, 128u), tc_smem_desc(bh + bo, B_LBO, 128u), IDESC, first);
+        if (split) {
+          tc_mma_tf32(tmem, tc_smem_desc(ah + ao, A_LBO, 128u), tc_smem_desc(bl + bo, B_LBO, 128u), IDESC, 1u);
+          tc_mma_tf32(tmem, tc_smem_desc(al + ao, A_LBO, 128u), tc_smem_desc(bh + bo, B_LBO, 128u), IDESC, 1u);
+        }
+      }
+      tc_commit(bar);
+    }
+    __syncwarp();
+    const bool landed = mbar_wait_bounded(bar, phase, spin);
+    phase ^= 1u;
+    ok = __syncthreads_and(landed) != 0;
+    if (!ok) break;
+  }
+  if (ok) {
+    tc_fence_after();
+    uint32_t v0[32], v1[32];
+    tc_ld32(tmem + ((uint32_t)(warp * 32) << 16), v0);
+    tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32u, v1);
+    const int m = m0 + warp * 32 + lane;
+    if (m < jb.M) {
+#pragma unroll
+      for (int j = 0; j < TNC; ++j) {
+        const int n = n0 + j;
+        if (n >= jb.N) break;
+        const float re = __uint_as_float(j < 16 ? v0[2 * j] : v1[2 * j - 32]);
+        const float im = __uint_as_float(j < 16 ? v0[2 * j + 1] : v1[2 * j + 1 - 32]);
+        c64& dst = Cm[(long long)m * jb.ldc + n];
+        const c64 val{jb.alpha * re, jb.alpha * im};
+        dst = jb.beta ? c64{dst.re + val.re, dst.im + val.im} : val;
+      }
+    }
+  } else {
+    (void)mbar_wait_bounded(bar, phase ^ 1u, 1LL << 30);
+    if (tid == 0) set_status(status, HS_ETIMEOUT, -6, tl.job);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tmem, TN);
+}
+
+}  // namespace
+
+int zgemm_tf32_batched(const std::vector<TcGemmJob>& jobs, int split, int* status, long long spin, cudaStream_t s) {
+  if (jobs.empty()) return HS_OK;
+  std::vector<TcGemmTile> tiles;
+  for (int t = 0; t < (int)jobs.size(); ++t)
+    for (int tm = 0; tm < (jobs[t].M + TM - 1) / TM; ++tm)
+      for (int tn = 0; tn < (jobs[t].N + TNC - 1) / TNC; ++tn) tiles.push_back({t, tm, tn});
+  TcGemmJob* dj = nullptr;
+  TcGemmTile* dt = nullptr;
+  HS_CUDA_TRY(cudaMalloc(&dj, jobs.size() * sizeof(TcGemmJob)));
+  if (cudaMalloc(&dt, tiles.size() * sizeof(TcGemmTile)) != cudaSuccess) {
+    cudaFree(dj);
+    return HS_ENOMEM;
+  }
+  cudaMemcpyAsync(dj, jobs.data(), jobs.size() * sizeof(TcGemmJob), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(TcGemmTile), cudaMemcpyHostToDevice, s);
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(zgemm_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  });
+  note_launch();
+  zgemm_tf32_kernel<<<(int)tiles.size(), 128, SMEM_BYTES, s>>>(dj, dt, split, status, spin);
+  cudaError_t e = cudaGetLastError();
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaFree(dj);
+  cudaFree(dt);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (e2 != cudaSuccess) return cuda_status(e2);
+  return HS_OK;
+}
+
+}  // namespace hs

@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 #include "hs_cnn.cuh"
 #include "hs_device.cuh"
+#include "hs_tc.cuh"
 
 namespace hs {
 namespace {
@@ -37,58 +38,7 @@ constexpr uint32_t TMEM_COLS = 32;
 // address a descriptor can form from this layout stays inside the allocation.
 constexpr uint32_t SMEM_BYTES = 160 * 1024;
 
-// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits
-// 4-5 = 1), A and B bfloat16 (bits 7-9 and 10-12 = 1), both K-major (bits 15,
-// 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NC >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-
-// Shared-memory matrix descriptor, no swizzle: start address, leading-
-// dimension byte offset (between core matrices along K), stride byte offset
-// (between core matrices along M or N), all >> 4; version 1 at bit 46.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// 32 consecutive accumulator columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
+constexpr uint32_t IDESC = tc_idesc(1u, TM, NC);   // bf16 A and B, FP32 accumulator
 
 // B operand of every K-step from the bf16-rounded FP32 weights W2[tap][ci][co]:
 // step s = (tap, half), 16-byte rows (co, 8 consecutive ci), channel group c
@@ -121,7 +71,7 @@ __global__ void __launch_bounds__(128, 1) conv2_tc_kernel(const __nv_bfloat16* _
     mbar_init(bar, 1);
     fence_mbar_init();
   }
-  if (warp == 0) tmem_alloc(tslot, TMEM_COLS);
+  if (warp == 0) tc_alloc(tslot, TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -153,11 +103,11 @@ __global__ void __launch_bounds__(128, 1) conv2_tc_kernel(const __nv_bfloat16* _
 #pragma unroll 1
       for (int s = 0; s < KSTEPS; ++s) {
         const int tap = s >> 1, h = s & 1, ky = tap / 3, kx = tap % 3;
-        const uint64_t ad = smem_desc(a_base + (uint32_t)(2 * h) * AG + (uint32_t)(ky * TWP + kx) * 16u, AG, 128u);
-        const uint64_t bd = smem_desc(b_base + (uint32_t)s * B_STEP, NC * 16u, 128u);
-        mma_bf16(tmem, ad, bd, s > 0 ? 1u : 0u);
+        const uint64_t ad = tc_smem_desc(a_base + (uint32_t)(2 * h) * AG + (uint32_t)(ky * TWP + kx) * 16u, AG, 128u);
+        const uint64_t bd = tc_smem_desc(b_base + (uint32_t)s * B_STEP, NC * 16u, 128u);
+        tc_mma_f16(tmem, ad, bd, IDESC, s > 0 ? 1u : 0u);
       }
-      mma_commit(bar);
+      tc_commit(bar);
     }
     __syncwarp();
     const bool landed = mbar_wait_bounded(bar, phase, spin);
@@ -166,7 +116,7 @@ __global__ void __launch_bounds__(128, 1) conv2_tc_kernel(const __nv_bfloat16* _
     if (!ok) break;
     tc_fence_after();
     uint32_t v[32];
-    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+    tc_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
     const int px = x0 + warp * 32 + lane;
     if (px < n) {
       __align__(16) __nv_bfloat162 o[CH / 2];
@@ -188,7 +138,7 @@ __global__ void __launch_bounds__(128, 1) conv2_tc_kernel(const __nv_bfloat16* _
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+  if (warp == 0) tc_dealloc(tmem, TMEM_COLS);
 }
 
 }  // namespace

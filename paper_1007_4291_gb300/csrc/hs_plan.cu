@@ -118,6 +118,7 @@ extern "C" int hs_default_options(hs_options* opt) {
   opt->reorth = 0;
   opt->spin_budget = 1LL << 30;
   opt->graphs = 1;
+  opt->frontal_gemm = 3;
   opt->tune_cache = nullptr;
   return HS_OK;
 }
@@ -197,6 +198,7 @@ static int prepare_plan3d(const double* c, double omega, int n, int pml_width, i
       opt.max_nrhs > 4096 || opt.restart < 1)
     return HS_EINVAL;
   if (opt.factor_prec != HS_C64 && opt.factor_prec != HS_C128) return HS_EINVAL;
+  if (opt.frontal_gemm != 0 && opt.frontal_gemm != 1 && opt.frontal_gemm != 3) return HS_EINVAL;
   const size_t N3 = (size_t)n * n * n;
   for (size_t k = 0; k < N3; ++k)
     if (!(c[k] > 0.0) || !std::isfinite(c[k])) return HS_EINVAL;

@@ -32,9 +32,10 @@ def relerr(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
-def plan3(c, omega, bp, b, dL, prec=hs.HS_C64, alpha=1.0, R=4):
+def plan3(c, omega, bp, b, dL, prec=hs.HS_C64, alpha=1.0, R=4, frontal=3):
     n = c.shape[0]
-    o = hs.hs_default_options(alpha=alpha, pml_C=C_PML, layers_per_step=dL, factor_prec=prec, max_nrhs=R)
+    o = hs.hs_default_options(alpha=alpha, pml_C=C_PML, layers_per_step=dL, factor_prec=prec, max_nrhs=R,
+                              frontal_gemm=frontal)
     return hs.hs_setup(c.ravel(), omega, n, 3, bp, b, o)
 
 
@@ -67,13 +68,20 @@ CASES = [
 ]
 
 
+# (factor precision, frontal GEMM mode, tolerance): FP32 FMA and 3xTF32 tensor
+# cores hold the complex64 bar; one TF32 pass (10-bit mantissa operands) is
+# held to 2e-2 and its error is printed
+MODES = [(hs.HS_C64, 0, 1e-4), (hs.HS_C64, 3, 1e-4), (hs.HS_C64, 1, 2e-2), (hs.HS_C128, 0, 1e-10)]
+
+
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("prec", [hs.HS_C64, hs.HS_C128])
-def test_apply3_matches_oracle(case, prec):
+@pytest.mark.parametrize("mode", MODES)
+def test_apply3_matches_oracle(case, mode):
     n, bp, b, dL, R = case
+    prec, frontal, tol = mode
     c = I.random_velocity(n, 5, dim=3)
     omega, alpha = 2 * np.pi * 1.5, 1.0
-    p = plan3(c, omega, bp, b, dL, prec=prec, alpha=alpha, R=R)
+    p = plan3(c, omega, bp, b, dL, prec=prec, alpha=alpha, R=R, frontal=frontal)
     try:
         r = I.random_rhs(n, R, 6, dim=3)
         io = prec
@@ -86,9 +94,9 @@ def test_apply3_matches_oracle(case, prec):
         z = zg.cpu().numpy().astype(np.complex128)
         st = H3.setup(c, omega, bp, b, dL, alpha, C_PML)
         ref = H3.apply(st, rg.cpu().numpy().astype(np.complex128))
-        tol = 1e-4 if prec == hs.HS_C64 else 1e-10
-        for k in range(R):
-            assert relerr(z[k], ref[k]) <= tol, (k, relerr(z[k], ref[k]))
+        err = max(relerr(z[k], ref[k]) for k in range(R))
+        print("3D apply n=%d prec=%d frontal=%d: max relative error %.3e" % (n, prec, frontal, err))
+        assert err <= tol
     finally:
         hs.hs_destroy(p)
 
