@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the comparator (complex128 sweep-GMRES), batched and 3D sections")
     return ap.parse_args()
 
 
@@ -221,6 +223,126 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU leg
+def comparator_fp64(args, wl, stream):
+    """The plain FP64 GPU sweep-GMRES on the same workload: complex128
+    factors and sweep, FP64 Krylov vectors (one warm-up, one timed solve)."""
+    import torch
+    from paper_1007_4291_gb300 import hs
+    n, R = wl["n"], args.nrhs
+    opt = hs.hs_default_options(alpha=wl["alpha"], pml_C=wl["C"], layers_per_step=args.dl, factor_prec=hs.HS_C128,
+                                chunk=args.chunk, max_nrhs=R, restart=args.restart)
+    c_host = np.ascontiguousarray(wl["c"].ravel())
+    f = torch.from_numpy(wl["f"]).to("cuda")
+    u = torch.zeros_like(f)
+    out = {}
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = hs.hs_setup(c_host, wl["omega"], n, 2, wl["bp"], wl["b"], opt, stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        u.zero_()
+        code, info = hs.hs_solve(plan, f, u, R, args.tol, 400, stream)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        hs.hs_destroy(plan)
+        out = {"what": "complex128 factors and sweep, FP64 FGMRES, same workload and tolerance",
+               "status": code, "time_to_1e6_s": t2 - t0, "setup_s": t1 - t0, "solve_s": t2 - t1,
+               "iterations": info["iterations"], "max_relres": info["max_relres"],
+               "ms_per_apply": info["t_apply_ms"] / max(info["applies"], 1)}
+    del f, u
+    torch.cuda.empty_cache()
+    hs.hs_release_workspace()
+    return out
+
+
+def batched_uneven(stream, nprob=32, nrhs=8):
+    """32 problems with n drawn (seed 2) from {255, 383, 511, 767, 1023},
+    omega/2pi = (n+1)/16, smooth random velocities (seeds 100+k), 8 point
+    sources each: one batched setup launch and one CUDA-graph application of
+    all 32 sweeps, against one-at-a-time setups and applies."""
+    import torch
+    from paper_1007_4291_gb300 import hs
+    from paper_1007_4291_gb300 import inputs as I
+    rng = np.random.default_rng(2)
+    ns = [int(x) for x in rng.choice([255, 383, 511, 767, 1023], size=nprob)]
+    cs = [I.random_velocity(n, 100 + k).ravel() for k, n in enumerate(ns)]
+    om = [2 * np.pi * (n + 1) / 16.0 for n in ns]
+    opt = hs.hs_default_options(alpha=2.0, pml_C=20.0, layers_per_step=12, max_nrhs=nrhs)
+    rs = [torch.from_numpy(I.point_sources(n, nrhs, 200 + k, 12)).to("cuda").to(torch.complex64)
+          for k, n in enumerate(ns)]
+    zs = [torch.empty_like(r) for r in rs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plans = hs.hs_setup_batched(cs, om, ns, 2, 12, 12, opt, stream)
+    torch.cuda.synchronize()
+    t_setup_b = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    singles = [hs.hs_setup(c, w, n, 2, 12, 12, opt, stream) for c, w, n in zip(cs, om, ns)]
+    torch.cuda.synchronize()
+    t_setup_s = time.perf_counter() - t0
+    for q in singles:
+        hs.hs_destroy(q)
+    nr = [nrhs] * nprob
+    hs.hs_apply_batched(plans, rs, zs, nr, hs.HS_C64, stream)      # capture
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        hs.hs_apply_batched(plans, rs, zs, nr, hs.HS_C64, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batched = e0.elapsed_time(e1) / reps
+    e0.record(stream)
+    for _ in range(reps):
+        for p, r, z in zip(plans, rs, zs):
+            hs.hs_apply(p, r, z, nrhs, hs.HS_C64, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / reps
+    st = max(hs.hs_last_device_status(p) for p in plans)
+    for p in plans:
+        hs.hs_destroy(p)
+    return {"problems": nprob, "nrhs_each": nrhs, "n": ns, "status": st,
+            "setup_batched_ms": t_setup_b * 1e3, "setup_one_at_a_time_ms": t_setup_s * 1e3,
+            "apply_graph_ms": t_batched, "apply_one_at_a_time_ms": t_seq,
+            "rhs_applies_per_s": nprob * nrhs / (t_batched / 1e3)}
+
+
+def three_d(stream, n=63, nrhs=16):
+    """3D: n = 63, omega/2pi = 4, PML 6, moving PML 5, d = 1, alpha = 1,
+    smooth random velocity, 16 point sources; time-to-1e-6 per frontal-GEMM
+    precision (3xTF32 and one-pass TF32 tensor cores, FP32 FMA, FP64)."""
+    import torch
+    from paper_1007_4291_gb300 import hs
+    from paper_1007_4291_gb300 import inputs as I
+    c = I.random_velocity(n, 0, dim=3).ravel()
+    f = torch.from_numpy(I.point_sources(n, nrhs, 1, 6, dim=3)).to("cuda")
+    omega = 2 * np.pi * 4.0
+    out = {"n": n, "nrhs": nrhs, "omega_over_2pi": 4.0}
+    for name, prec, mode in (("c64_3xtf32_tensor", hs.HS_C64, 3), ("c64_tf32_tensor", hs.HS_C64, 1),
+                             ("c64_fp32_fma", hs.HS_C64, 0), ("c128_fp64", hs.HS_C128, 0)):
+        opt = hs.hs_default_options(alpha=1.0, pml_C=20.0, layers_per_step=1, factor_prec=prec, max_nrhs=nrhs,
+                                    frontal_gemm=mode)
+        best = None
+        for rep in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan = hs.hs_setup(c, omega, n, 3, 6, 5, opt, stream)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            u = torch.zeros_like(f)
+            code, info = hs.hs_solve(plan, f, u, nrhs, 1e-6, 200, stream)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            hs.hs_destroy(plan)
+            best = {"status": code, "time_to_1e6_s": t2 - t0, "setup_s": t1 - t0, "solve_s": t2 - t1,
+                    "iterations": info["iterations"], "max_relres": info["max_relres"],
+                    "ms_per_apply": info["t_apply_ms"] / max(info["applies"], 1)}
+        out[name] = best
+    return out
+
+
 def run_ours(args):
     import torch
     import __graft_entry__ as G
@@ -355,6 +477,10 @@ def run_ours(args):
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["comparator_fp64"] = comparator_fp64(args, wl, stream)
+        line["batched_uneven"] = batched_uneven(stream)
+        line["three_d"] = three_d(stream)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = oracle_sample(wl, R, max(it))
     if rank == 0:
