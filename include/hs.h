@@ -247,6 +247,13 @@ int hs_cnn_gradient(hs_cnn* net, const void* x, const void* e, int nrhs, int n, 
  * step (synchronises the stream). */
 int hs_cnn_train_step(hs_cnn* net, const void* x, const void* e, int nrhs, int n, int dtype, double lr,
                       double* loss, void* stream);
+/* One Adam step on the residual loss L = mean over RHS of |A c - rho|^2 / |rho|^2,
+ * c = s N(x/s), for sweep outputs x = M_alpha v and their residuals
+ * rho = v - A x (complex64 device vectors of plan's n x n grid, ABI layout;
+ * A is the plan's Eq. helmd operator): the quantity the solver's judge
+ * compares.  *loss (if not NULL) gets L before the step (synchronises). */
+int hs_cnn_train_step_residual(hs_cnn* net, hs_plan* plan, const void* x, const void* rho, int nrhs, double lr,
+                               double* loss, void* stream);
 /* Wait for `stream` and report a device error recorded by the network's
  * tensor-core kernel (HS_ETIMEOUT after an expired bounded wait). */
 int hs_cnn_sync(hs_cnn* net, void* stream);

@@ -27,7 +27,10 @@ each layer's stored activations to bfloat16 (round to nearest even), the
 storage precision of the GPU kernels, so that the two can be compared
 element by element; the arithmetic stays float64.
 
-Pins: the convolution against ``scipy.signal.correlate2d``, the gradients
+A second loss, the one the solver's judge measures, fits the correction in
+the residual norm: for rho = v - A x, mean over pairs of |A c - rho|^2 / |rho|^2.
+
+Pins: the convolution against ``scipy.signal.correlate2d``, both gradients
 against central finite differences (FP64), the first Adam step against its
 closed form (every parameter moves by lr in the direction -sign(g)).
 """
@@ -144,6 +147,31 @@ def loss_and_grad(theta, rs, es, bf16=False):
         for name, v in (("W1", gW1), ("b1", gb1), ("W2", gW2), ("b2", gb2), ("W3", gW3), ("b3", gb3)):
             g[name] += v
     return L / npts, pack(g) / npts
+
+
+def residual_loss_and_grad(theta, xs, rhos, apply_A, bf16=False):
+    """L = mean over pairs of |A c - rho|^2 / |rho|^2 with c = s N(x/s),
+    s = rms(x), and its gradient (A complex symmetric: dL/dc = 2 conj(A conj(d))
+    / (|rho|^2 R) for d = A c - rho; dL/do = s (Re, Im) of that)."""
+    g = {name: np.zeros(shp) for name, shp in SHAPES}
+    L, R = 0.0, len(xs)
+    for x, rho in zip(xs, rhos):
+        s = rms(x)
+        o, c = forward(theta, image(x, s), bf16)
+        corr = s * (o[..., 0] + 1j * o[..., 1])
+        d = apply_A(corr) - rho
+        nr = float(np.sum(np.abs(rho) ** 2))
+        L += float(np.sum(np.abs(d) ** 2)) / nr / R
+        G = 2.0 * np.conj(apply_A(np.conj(d))) / (nr * R)
+        do = s * np.stack([G.real, G.imag], axis=-1)
+        dh2, gW3, gb3 = conv3x3_backward(c["h2"], c["W3"], do)
+        da2 = dh2 * (c["h2"] > 0)
+        dh1, gW2, gb2 = conv3x3_backward(c["h1"], c["W2"], da2)
+        da1 = dh1 * (c["h1"] > 0)
+        _, gW1, gb1 = conv3x3_backward(c["x"], c["W1"], da1)
+        for name, v in (("W1", gW1), ("b1", gb1), ("W2", gW2), ("b2", gb2), ("W3", gW3), ("b3", gb3)):
+            g[name] += v
+    return L, pack(g)
 
 
 class Adam:

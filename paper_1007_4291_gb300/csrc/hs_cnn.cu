@@ -382,6 +382,65 @@ __global__ void __launch_bounds__(288) bwd_weight_kernel(const __nv_bfloat16* __
   if (t < COUT) atomicAdd(grad + boff + t, bacc);
 }
 
+// ------------------------------------------------------------------ residual loss
+// Training toward the FP64-residual judge: for a sweep output x = M v with
+// residual rho = v - A x, the correction c = s N(x/s) should make A c close to
+// rho.  L = mean over RHS of |A c - rho|^2 / |rho|^2.  With d = A c - rho and
+// A complex symmetric, dL/dc = 2 A^H d / (|rho|^2 R) = 2 conj(A conj(d)) / (...).
+__global__ void resid_norm_kernel(const c64* __restrict__ rho, int n2, double* nrm) {
+  const int k = blockIdx.y;
+  double acc = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n2; p += gridDim.x * blockDim.x) {
+    const c64 v = rho[(long long)k * n2 + p];
+    acc += (double)v.re * v.re + (double)v.im * v.im;
+  }
+  __shared__ double red[8];
+  for (int m = 16; m > 0; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += red[q];
+    atomicAdd(&nrm[k], t);
+  }
+}
+
+// d = A c - rho; stores conj(d) in out and accumulates the loss
+__global__ void resid_diff_kernel(const c64* __restrict__ ac, const c64* __restrict__ rho, c64* __restrict__ out,
+                                  int n2, int R, const double* nrm, double* loss) {
+  const int k = blockIdx.y;
+  double acc = 0.0;
+  const double w = nrm[k] > 0.0 ? 1.0 / (nrm[k] * R) : 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n2; p += gridDim.x * blockDim.x) {
+    const long long i = (long long)k * n2 + p;
+    const float dr = ac[i].re - rho[i].re, di = ac[i].im - rho[i].im;
+    out[i] = c64{dr, -di};
+    acc += ((double)dr * dr + (double)di * di) * w;
+  }
+  __shared__ double red[8];
+  for (int m = 16; m > 0; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += red[q];
+    atomicAdd(loss, t);
+  }
+}
+
+// dL/do = s * 2 conj(g') / (|rho|^2 R), g' = A conj(d), as the two channels
+__global__ void resid_dout_kernel(const c64* __restrict__ g, int n2, int R, const double* sums, const double* nrm,
+                                  float* __restrict__ dout) {
+  const int k = blockIdx.y;
+  const double s2 = sums[k] / n2;
+  const double sk = s2 > 0.0 ? sqrt(s2) : 0.0;
+  const double w = nrm[k] > 0.0 ? 2.0 * sk / (nrm[k] * R) : 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n2; p += gridDim.x * blockDim.x) {
+    const long long i = (long long)k * n2 + p;
+    reinterpret_cast<float2*>(dout)[i] = make_float2((float)(w * g[i].re), (float)(-w * g[i].im));
+  }
+}
+
 // ------------------------------------------------------------------ Adam
 __global__ void adam_kernel(float* theta, float* wq, float* grad, float* m, float* v, int np, float lr, float c1,
                             float c2) {
@@ -415,7 +474,7 @@ int Cnn::reserve(int R, int n) {
   cap_px = 0; cap_r = 0;
   HS_CUDA_TRY(cudaMalloc(&h1, px * CH * sizeof(__nv_bfloat16)));
   HS_CUDA_TRY(cudaMalloc(&h2, px * CH * sizeof(__nv_bfloat16)));
-  HS_CUDA_TRY(cudaMalloc(&sums, (R + 1) * sizeof(double)));
+  HS_CUDA_TRY(cudaMalloc(&sums, (2 * R + 2) * sizeof(double)));
   cap_px = px;
   cap_r = R;
   return HS_OK;
@@ -426,18 +485,20 @@ int Cnn::reserve_train(int R, int n) {
   const size_t px = (size_t)R * n * n;
   if (da1 && px <= cap_train) return HS_OK;
   cudaDeviceSynchronize();
-  cudaFree(dout); cudaFree(da2); cudaFree(da1);
+  cudaFree(dout); cudaFree(da2); cudaFree(da1); cudaFree(rbuf);
   dout = da2 = da1 = nullptr;
+  rbuf = nullptr;
   cap_train = 0;
   HS_CUDA_TRY(cudaMalloc(&dout, px * 2 * sizeof(float)));
   HS_CUDA_TRY(cudaMalloc(&da2, px * CH * sizeof(float)));
   HS_CUDA_TRY(cudaMalloc(&da1, px * CH * sizeof(float)));
+  HS_CUDA_TRY(cudaMalloc(&rbuf, 3 * px * sizeof(c64)));
   cap_train = px;
   return HS_OK;
 }
 
 Cnn::~Cnn() {
-  void* ptrs[] = {theta, wq, grad, m, v, h1, h2, dout, da2, da1, sums, w2tc, status};
+  void* ptrs[] = {theta, wq, grad, m, v, h1, h2, dout, da2, da1, sums, w2tc, status, rbuf};
   for (void* q : ptrs) if (q) cudaFree(q);
 }
 
@@ -482,16 +543,25 @@ int forward_t(Cnn& c, const T* r, Z* z, long long sp, long long sk, int R, int n
 }
 
 template <typename T>
+int backward_t(Cnn& c, const T* r, long long sp, long long sk, int R, int n, cudaStream_t s);
+
+template <typename T>
 int gradient_t(Cnn& c, const T* r, const T* e, long long sp, long long sk, int R, int n, cudaStream_t s) {
   HS_TRY_INT(c.reserve_train(R, n));
+  cudaMemsetAsync(c.grad, 0, CNN_NPARAM * sizeof(float), s);
+  const double inv_npts = 1.0 / ((double)R * n * n);
+  HS_TRY_INT((forward_t<T, c64, true>(c, r, nullptr, sp, sk, R, n, e, inv_npts, false, s)));
+  return backward_t<T>(c, r, sp, sk, R, n, s);
+}
+
+// Backward pass from dL/do in c.dout (the forward's activations in c.h1/h2).
+template <typename T>
+int backward_t(Cnn& c, const T* r, long long sp, long long sk, int R, int n, cudaStream_t s) {
   static std::once_flag once;
   std::call_once(once, [] {
     cudaFuncSetAttribute(bwd_weight_kernel<CH, CH, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)bwd_weight_smem<CH, CH>());
   });
-  cudaMemsetAsync(c.grad, 0, CNN_NPARAM * sizeof(float), s);
-  const double inv_npts = 1.0 / ((double)R * n * n);
-  HS_TRY_INT((forward_t<T, c64, true>(c, r, nullptr, sp, sk, R, n, e, inv_npts, false, s)));
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -614,6 +684,45 @@ extern "C" int hs_cnn_train_step(hs_cnn* net, const void* r, const void* e, int 
   adam_kernel<<<(CNN_NPARAM + 255) / 256, 256, 0, s>>>(c.theta, c.wq, c.grad, c.m, c.v, CNN_NPARAM, (float)lr, c1, c2);
   if (loss) {
     HS_CUDA_TRY(cudaMemcpyAsync(loss, c.sums + nrhs, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HS_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  cudaError_t ce = cudaGetLastError();
+  return ce == cudaSuccess ? HS_OK : cuda_status(ce);
+}
+
+extern "C" int hs_cnn_train_step_residual(hs_cnn* net, hs_plan* plan, const void* x, const void* rho, int nrhs,
+                                          double lr, double* loss, void* stream) {
+  if (!net || !plan || !x || !rho || !(lr > 0.0) || nrhs < 1) return HS_EINVAL;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (p.dim != 2 || nrhs > p.max_nrhs) return HS_EINVAL;
+  Cnn& c = *reinterpret_cast<Cnn*>(net);
+  const int n = p.n, n2 = n * n, R = nrhs;
+  HS_TRY_INT(c.reserve_train(R, n));
+  cudaStream_t s = (cudaStream_t)stream;
+  c64* cb = static_cast<c64*>(c.rbuf);
+  c64* ab = cb + (size_t)R * n2;
+  c64* db = ab + (size_t)R * n2;
+  double* nrm = c.sums + R + 1;
+  double* lossd = c.sums + 2 * R + 1;
+  cudaMemsetAsync(c.grad, 0, CNN_NPARAM * sizeof(float), s);
+  cudaMemsetAsync(cb, 0, (size_t)R * n2 * sizeof(c64), s);
+  const long long sp = 1, sk = n2;
+  HS_TRY_INT((forward_t<c64, c64, false>(c, (const c64*)x, cb, sp, sk, R, n, nullptr, 0.0, false, s)));
+  cudaMemsetAsync(nrm, 0, (R + 1) * sizeof(double), s);
+  const dim3 g2(std::min((n2 + 255) / 256, 64), R);
+  note_launch(3);
+  resid_norm_kernel<<<g2, 256, 0, s>>>((const c64*)rho, n2, nrm);
+  HS_TRY_INT(matvec_abi(p, cb, ab, R, HS_C64, s));                       // A c
+  resid_diff_kernel<<<g2, 256, 0, s>>>(ab, (const c64*)rho, db, n2, R, nrm, lossd);
+  HS_TRY_INT(matvec_abi(p, db, ab, R, HS_C64, s));                       // A conj(d)
+  resid_dout_kernel<<<g2, 256, 0, s>>>(ab, n2, R, c.sums, nrm, c.dout);
+  HS_TRY_INT(backward_t<c64>(c, (const c64*)x, sp, sk, R, n, s));
+  c.t += 1;
+  const float c1 = (float)(1.0 - std::pow(0.9, c.t)), c2 = (float)(1.0 - std::pow(0.999, c.t));
+  note_launch();
+  adam_kernel<<<(CNN_NPARAM + 255) / 256, 256, 0, s>>>(c.theta, c.wq, c.grad, c.m, c.v, CNN_NPARAM, (float)lr, c1, c2);
+  if (loss) {
+    HS_CUDA_TRY(cudaMemcpyAsync(loss, lossd, sizeof(double), cudaMemcpyDeviceToHost, s));
     HS_CUDA_TRY(cudaStreamSynchronize(s));
   }
   cudaError_t ce = cudaGetLastError();

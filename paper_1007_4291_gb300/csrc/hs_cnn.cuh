@@ -29,12 +29,13 @@ struct Cnn {
   // workspace, grown on demand
   __nv_bfloat16* h1 = nullptr;   // [R][n][n][32]
   __nv_bfloat16* h2 = nullptr;
-  double* sums = nullptr;        // [R] sums of |r|^2, then the loss
+  double* sums = nullptr;        // [R] sums of |r|^2, the loss, [R] residual norms, residual loss
   float* dout = nullptr;         // [R][n][n][2]  dL/do
   float* da2 = nullptr;          // [R][n][n][32] dL/da2
   float* da1 = nullptr;          // [R][n][n][32] dL/da1
   void* w2tc = nullptr;          // layer-2 weights in the tensor-core operand layout
   int* status = nullptr;         // device status word of the tensor-core kernel (expired waits)
+  void* rbuf = nullptr;          // residual training: c, A c, A conj(d) (complex64, ABI layout)
   int w2tc_version = -1;         // Adam step the packed copy was made from
   size_t cap_px = 0, cap_train = 0;
   int cap_r = 0;

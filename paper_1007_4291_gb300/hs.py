@@ -22,7 +22,7 @@ EXPORTED = ["hs_default_options", "hs_setup", "hs_setup_batched", "hs_apply", "h
             "hs_apply_noalloc", "hs_autotune", "hs_matvec", "hs_solve", "hs_sync", "hs_last_device_status",
             "hs_plan_bytes", "hs_release_workspace", "hs_kernel_launches", "hs_destroy", "hs_strerror",
             "hs_cnn_create", "hs_cnn_get_params", "hs_cnn_set_mode", "hs_cnn_apply", "hs_cnn_gradient",
-            "hs_cnn_train_step", "hs_cnn_sync", "hs_cnn_destroy", "hs_attach_cnn"]
+            "hs_cnn_train_step", "hs_cnn_train_step_residual", "hs_cnn_sync", "hs_cnn_destroy", "hs_attach_cnn"]
 HS_CNN_NPARAM = 10434
 
 
@@ -88,6 +88,7 @@ def load(path=None):
     lib.hs_cnn_train_step.argtypes = [vp, vp, vp, i, i, i, d, ctypes.POINTER(d), vp]
     lib.hs_cnn_destroy.argtypes = [vp]
     lib.hs_cnn_sync.argtypes = [vp, vp]
+    lib.hs_cnn_train_step_residual.argtypes = [vp, vp, vp, vp, i, d, ctypes.POINTER(d), vp]
     lib.hs_attach_cnn.argtypes = [vp, vp]
     lib.hs_kernel_launches.argtypes = []
     lib.hs_kernel_launches.restype = ll
@@ -235,6 +236,13 @@ def hs_cnn_train_step(net, r, e, nrhs, n, dtype, lr, stream=None):
     loss = ctypes.c_double()
     _check(load().hs_cnn_train_step(net, _ptr(r), _ptr(e), int(nrhs), int(n), int(dtype), float(lr),
                                     ctypes.byref(loss), _stream(stream)), "hs_cnn_train_step")
+    return loss.value
+
+
+def hs_cnn_train_step_residual(net, plan, x, rho, nrhs, lr, stream=None):
+    loss = ctypes.c_double()
+    _check(load().hs_cnn_train_step_residual(net, plan, _ptr(x), _ptr(rho), int(nrhs), float(lr), ctypes.byref(loss),
+                                             _stream(stream)), "hs_cnn_train_step_residual")
     return loss.value
 
 

@@ -6,10 +6,12 @@ itself: v runs over the first Arnoldi vectors of right-preconditioned GMRES
 started from Gaussian point sources (the vectors the preconditioner is
 applied to inside FGMRES); A^{-1} v comes from hs_solve to a tight
 tolerance, M_alpha v from hs_apply.
-Training runs the library's own forward, backward and Adam kernels
-(hs_cnn_train_step); evaluation reports the relative error of the corrected
-preconditioner on held-out pairs and FGMRES iteration counts with and
-without the network.
+Training runs the library's own forward, backward and Adam kernels.  The
+default loss is the residual one (hs_cnn_train_step_residual): for x = M v and
+rho = v - A x it fits A c to rho, the quantity the solver's judge compares,
+and needs no solves.  The error loss (hs_cnn_train_step) fits c to the sweep
+error e.  Evaluation reports the held-out ratio |rho - A c| / |rho| (or the
+error ratio) and FGMRES iteration counts with and without the network.
 
     python -m paper_1007_4291_gb300.train_cnn --n 511 --pairs 2048 --steps 600 --out weights.npy
 """
@@ -64,6 +66,88 @@ def make_pairs(n, seeds, nrhs, bp=12, b=12, layers=12, tol=1e-9, src_seed0=1000,
         finally:
             hs.hs_destroy(plan)
     return torch.cat(xs), torch.cat(es)
+
+
+class ResidualData:
+    """Per field: the plan (kept for its operator A), sweep outputs x = M v
+    and residuals rho = v - A x of the first Arnoldi vectors v of plain GMRES
+    from point sources (complex64 device tensors).  No solves are needed:
+    this is the quantity the solver's judge compares."""
+
+    def __init__(self, n, seeds, nrhs, bp=12, b=12, layers=12, krylov=6, src_seed0=1000):
+        import torch
+
+        from . import hs
+        from . import inputs as I
+
+        self.n, self.fields = n, []
+        for seed in seeds:
+            c = I.random_velocity(n, seed)
+            o = hs.hs_default_options(layers_per_step=layers, max_nrhs=nrhs, factor_prec=hs.HS_C64)
+            plan = hs.hs_setup(c.ravel(), omega_of(n), n, 2, bp, b, o)
+            f = torch.from_numpy(I.point_sources(n, nrhs, src_seed0 + seed, bp)).to("cuda")
+            V = [f / torch.linalg.vector_norm(f.reshape(nrhs, -1), dim=1).reshape(nrhs, 1, 1)]
+            xs, rhos = [], []
+            for j in range(krylov):
+                v = V[-1].contiguous()
+                x = torch.empty_like(v)
+                hs.hs_apply(plan, v, x, nrhs, hs.HS_C128)
+                ax = torch.empty_like(v)
+                hs.hs_matvec(plan, x, ax, nrhs, hs.HS_C128)
+                xs.append(x.to(torch.complex64))
+                rhos.append((v - ax).to(torch.complex64))
+                w = ax
+                for _ in range(2):
+                    for vi in V:
+                        h = (vi.conj() * w).reshape(nrhs, -1).sum(dim=1).reshape(nrhs, 1, 1)
+                        w = w - h * vi
+                V.append(w / torch.linalg.vector_norm(w.reshape(nrhs, -1), dim=1).reshape(nrhs, 1, 1))
+            self.fields.append((plan, torch.cat(xs), torch.cat(rhos)))
+
+    def close(self):
+        from . import hs
+        for plan, _, _ in self.fields:
+            hs.hs_destroy(plan)
+        self.fields = []
+
+
+def train_residual(net, data, steps, batch=8, lr=1e-3, seed=0, log_every=0):
+    import torch
+
+    from . import hs
+
+    g = torch.Generator().manual_seed(seed)
+    losses = []
+    for it in range(steps):
+        k = int(torch.randint(len(data.fields), (1,), generator=g))
+        plan, x, rho = data.fields[k]
+        idx = torch.randperm(x.shape[0], generator=g)[:batch].to(x.device)
+        losses.append(hs.hs_cnn_train_step_residual(net, plan, x[idx].contiguous(), rho[idx].contiguous(), batch, lr))
+        if log_every and it % log_every == 0:
+            print("step %d residual loss %.5g" % (it, losses[-1]), flush=True)
+    return losses
+
+
+def residual_ratio(net, data, batch=16):
+    """Per direction |rho - A c| / |rho| (the judge keeps c where it is < 1):
+    returns (mean ratio, fraction of directions kept)."""
+    import torch
+
+    from . import hs
+
+    ratios = []
+    for plan, x, rho in data.fields:
+        for k in range(0, x.shape[0], batch):
+            xb, rb = x[k:k + batch].contiguous(), rho[k:k + batch]
+            c = torch.zeros_like(xb)
+            hs.hs_cnn_apply(net, xb, c, xb.shape[0], data.n, hs.HS_C64)
+            ac = torch.empty_like(c)
+            hs.hs_matvec(plan, c, ac, c.shape[0], hs.HS_C64)
+            num = torch.linalg.vector_norm((rb - ac).reshape(rb.shape[0], -1), dim=1)
+            den = torch.linalg.vector_norm(rb.reshape(rb.shape[0], -1), dim=1)
+            ratios.append((num / den).double().cpu())
+    r = torch.cat(ratios)
+    return float(r.mean()), float((r < 1).double().mean())
 
 
 def corrected_error(net, r, e, n, batch=16):
@@ -138,6 +222,8 @@ def main(argv=None):
     ap.add_argument("--out", default=None, help="save the trained parameters (.npy)")
     ap.add_argument("--eval-n", type=int, nargs="*", default=[511, 1023])
     ap.add_argument("--report", default=None, help="write the JSON report to this file too")
+    ap.add_argument("--loss", choices=["residual", "error"], default="residual",
+                    help="residual: |A c - rho| (what the solver's judge compares); error: |c - e|")
     args = ap.parse_args(argv)
     import torch
 
@@ -146,6 +232,37 @@ def main(argv=None):
 
     build.build()
     nfields = max(1, args.pairs // (args.krylov * args.nrhs))
+    if args.loss == "residual":
+        t0 = time.perf_counter()
+        data = ResidualData(args.n, list(range(1000, 1000 + nfields)), args.nrhs, krylov=args.krylov)
+        held = ResidualData(args.n, [5000], min(args.nrhs, 16), krylov=args.krylov)
+        t_data = time.perf_counter() - t0
+        net = hs.hs_cnn_create(I.cnn_init_params(0))
+        try:
+            hs.hs_cnn_set_mode(net, 1)
+            before = residual_ratio(net, held)
+            t0 = time.perf_counter()
+            losses = train_residual(net, data, args.steps, args.batch, args.lr, log_every=100)
+            torch.cuda.synchronize()
+            t_train = time.perf_counter() - t0
+            after = residual_ratio(net, held)
+            if args.out:
+                np.save(args.out, hs.hs_cnn_get_params(net))
+            report = {"loss": "residual", "n": args.n, "pairs": sum(int(x.shape[0]) for _, x, _ in data.fields),
+                      "steps": args.steps, "data_s": t_data, "train_s": t_train, "loss_first": losses[0],
+                      "loss_last": float(np.mean(losses[-20:])),
+                      "heldout_residual_ratio_before": before[0], "heldout_kept_before": before[1],
+                      "heldout_residual_ratio_after": after[0], "heldout_kept_after": after[1],
+                      "fgmres": {str(m): iterations(m, 5000 + m, net) for m in args.eval_n}}
+            print(json.dumps(report))
+            if args.report:
+                with open(args.report, "w") as fh:
+                    json.dump(report, fh, indent=1)
+        finally:
+            hs.hs_cnn_destroy(net)
+            data.close()
+            held.close()
+        return
     t0 = time.perf_counter()
     r, e = make_pairs(args.n, list(range(1000, 1000 + nfields)), args.nrhs, krylov=args.krylov)
     rv, ev = make_pairs(args.n, [5000], min(args.nrhs, 16), krylov=args.krylov)

@@ -110,6 +110,36 @@ def test_first_adam_step_moves_each_parameter_by_lr():
         hs.hs_cnn_destroy(net)
 
 
+def test_residual_step_matches_oracle_loss_and_gradient_signs():
+    """hs_cnn_train_step_residual: its loss equals the oracle's and its first
+    Adam step moves every parameter with a clear gradient by -lr sign(g)."""
+    from oracle import helmholtz2d as H
+    n, R, lr = 31, 2, 1e-3
+    c = I.random_velocity(n, 4)
+    omega, bp = 2 * np.pi * 2.0, 5
+    o = hs.hs_default_options(alpha=2.0, pml_C=20.0, layers_per_step=2, chunk=8, max_nrhs=R)
+    plan = hs.hs_setup(c.ravel(), omega, n, 2, bp, bp, o)
+    th = theta32(21)
+    net = hs.hs_cnn_create(th)
+    try:
+        x = torch.from_numpy(I.random_rhs(n, R, 22)).to("cuda").to(torch.complex64)
+        rho = torch.from_numpy(I.random_rhs(n, R, 23)).to("cuda").to(torch.complex64) * 1e3
+        loss = hs.hs_cnn_train_step_residual(net, plan, x, rho, R, lr)
+        th1 = hs.hs_cnn_get_params(net)
+        coef = H.stencil_coefficients(c, omega, bp, 20.0, alpha=0.0)
+        apply_A = lambda z: H.apply_stencil(coef, z)
+        xin = list(x.cpu().numpy().astype(np.complex128))
+        rin = list(rho.cpu().numpy().astype(np.complex128))
+        L, g = K.residual_loss_and_grad(th.astype(np.float64), xin, rin, apply_A, bf16=True)
+        assert abs(loss - L) <= 1e-3 * L, (loss, L)
+        big = np.abs(g) > 1e-3 * np.abs(g).max()
+        d = (th1 - th).astype(np.float64)
+        assert np.mean(np.sign(d[big]) == -np.sign(g[big])) > 0.99
+    finally:
+        hs.hs_cnn_destroy(net)
+        hs.hs_destroy(plan)
+
+
 def test_training_learns_a_teacher_network():
     """The student (another random init) fits a teacher's corrections."""
     n, R = 32, 8

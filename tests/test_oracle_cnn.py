@@ -59,6 +59,27 @@ def test_gradient_matches_central_differences():
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
 
 
+def test_residual_gradient_matches_central_differences():
+    """The residual loss through a complex symmetric A (a random one here)."""
+    rng = np.random.default_rng(12)
+    theta = rand_theta(13)
+    n = 5
+    M = rng.standard_normal((n * n, n * n)) + 1j * rng.standard_normal((n * n, n * n))
+    M = M + M.T
+    apply_A = lambda z: (M @ z.ravel()).reshape(n, n)
+    xs = [rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) for _ in range(2)]
+    rhos = [rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) for _ in range(2)]
+    L, g = K.residual_loss_and_grad(theta, xs, rhos, apply_A)
+    idx = np.concatenate([rng.choice(K.NPARAM, 30, replace=False), [K.NPARAM - 1, K.NPARAM - 2]])
+    eps = 1e-6
+    for i in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += eps
+        tm[i] -= eps
+        fd = (K.residual_loss_and_grad(tp, xs, rhos, apply_A)[0] - K.residual_loss_and_grad(tm, xs, rhos, apply_A)[0]) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
 def test_adam_first_step_closed_form():
     """After one step m_hat = g and v_hat = g^2, so each parameter moves by
     lr * g / (|g| + eps): -lr sign(g) up to eps."""
