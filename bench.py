@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--krylov-basis", type=int, default=1, choices=[0, 1],
+                    help="1: FP32-basis FGMRES cycles restarted from the double-float residual (default); "
+                         "0: double-float basis")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the comparator (complex128 sweep-GMRES), batched and 3D sections")
     return ap.parse_args()
@@ -76,6 +79,9 @@ def config_dict(args, wl):
         "n": wl["n"], "nrhs": args.nrhs, "omega_over_2pi": wl["freq"], "pml_width": wl["bp"],
         "moving_pml_width": wl["b"], "layers_per_step": args.dl, "factor_prec": "c%d" % args.prec,
         "restart": args.restart, "tol": args.tol,
+        "krylov": ("FP32 Arnoldi basis in refinement cycles (inner 1e-4) restarted from the double-float true "
+                   "residual; iterate and residual double-float" if args.krylov_basis == 1 and args.prec == 64
+                   else "double-float Arnoldi basis, iterate and residual" if args.prec == 64 else "FP64 throughout"),
         "l2": "inputs larger than L2 (f is %.1f GB, factors and Krylov basis tens of GB)" %
               (wl["f"].nbytes / 1e9),
         "step": "hs_setup + hs_solve (+ hs_destroy)",
@@ -363,7 +369,7 @@ def run_ours(args):
     wl = workload(args)
     n, R = wl["n"], args.nrhs
     opt = hs.hs_default_options(alpha=wl["alpha"], pml_C=wl["C"], layers_per_step=args.dl, factor_prec=args.prec,
-                                chunk=args.chunk, max_nrhs=R, restart=args.restart)
+                                chunk=args.chunk, max_nrhs=R, restart=args.restart, krylov_basis=args.krylov_basis)
     stream = torch.cuda.current_stream()
     c_host = np.ascontiguousarray(wl["c"].ravel())
     f_dev = torch.from_numpy(wl["f"]).to("cuda")

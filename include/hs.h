@@ -60,6 +60,13 @@ typedef struct {
   int graphs;            /* 1: hs_apply replays the stage chain of the sweep as a CUDA graph
                             (captured on first use per nrhs); 0: direct launches.  hs_solve
                             sweeps a different Krylov vector at every step and launches directly. default 1 */
+  int krylov_basis;      /* 2D complex64 plans: 0 FGMRES with a double-float Arnoldi basis; 1 mixed-
+                            precision refinement: cycles of FGMRES with an FP32 basis (FP32
+                            Gram-Schmidt) restarted from the double-float true residual, x
+                            updated in double-float (a network attached with hs_attach_cnn
+                            uses mode 0).                                                    default 1 */
+  double inner_tol;      /* refinement cycles end when their residual estimate has fallen by this
+                            factor (or below tol).                                             default 1e-4 */
   int frontal_gemm;      /* 3D setup, frontal Schur updates of complex64 factors: 0 CUDA-core FP32
                             FMA, 1 TF32 tensor cores (one pass), 3 3xTF32 tensor cores (split
                             operands, FP32-level accuracy).  Complex128 factors use FP64 FMA.   default 3 */
@@ -193,8 +200,9 @@ int hs_matvec(hs_plan* plan, const void* x, void* y, int nrhs, int dtype, void* 
 /*
  * hs_solve -- solve A u = f for nrhs RHS with right-preconditioned flexible
  * GMRES(m) (Sec. 2.3 uses GMRES on M_alpha A; the flexible right form lets the
- * true residual decide): FP64 Arnoldi (Gram-Schmidt) and true residual,
- * preconditioner in the plan's factor precision.  The RHS advance in lock
+ * true residual decide): FP64-class true residual and iterate (double-float
+ * for complex64 2D plans, FP64 otherwise), Arnoldi basis per
+ * opt.krylov_basis, preconditioner in the plan's factor precision.  The RHS advance in lock
  * step; each stops when ||f - A u|| <= tol ||f|| (FP64, recomputed at every
  * restart and at the end).
  * f, u     device HS_C128 vectors; u is the initial guess on entry and the

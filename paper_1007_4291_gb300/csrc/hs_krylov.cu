@@ -89,6 +89,29 @@ struct DF64 {
   static __device__ __forceinline__ c128 out_c128(V v) { return cdf_to_c128(v); }
 };
 
+// Single precision, for the basis of the refinement mode: FP32 products with
+// per-thread FP32 partial sums, combined in FP64 across threads and CTAs.
+struct F32 {
+  using V = c64;
+  using A = c64;
+  using N = float;
+  static __device__ __forceinline__ A zero() { return c64{0.f, 0.f}; }
+  static __device__ __forceinline__ void acc_conj(A& acc, V v, V w) { cfmaconj(acc, v, w); }
+  static __device__ __forceinline__ void norm_zero(N& n) { n = 0.f; }
+  static __device__ __forceinline__ void norm_acc(N& nrm, V w) { nrm = fmaf(w.re, w.re, fmaf(w.im, w.im, nrm)); }
+  static __device__ __forceinline__ double norm_out(N n) { return (double)n; }
+  static __device__ __forceinline__ c128 to_c128(A a) { return c128{(double)a.re, (double)a.im}; }
+  static __device__ __forceinline__ V coef(c128 h) { return c64{(float)h.re, (float)h.im}; }
+  static __device__ __forceinline__ void sub_prod(V& w, V h, V v) { cfms(w, h, v); }
+  template <typename ZT>
+  static __device__ __forceinline__ void add_prod_z(V& x, V y, cplx<ZT> z) {
+    cfma(x, y, c64{(float)z.re, (float)z.im});
+  }
+  static __device__ __forceinline__ c64 to_c64(V v) { return v; }
+  static __device__ __forceinline__ V from_c128(c128 v) { return c64{(float)v.re, (float)v.im}; }
+  static __device__ __forceinline__ c128 out_c128(V v) { return c128{(double)v.re, (double)v.im}; }
+};
+
 // ---------------------------------------------------------------- kernels
 // part[cta][i][r] = sum over this CTA's points of conj(V_i) w ; slot nv holds |w|^2.
 template <typename AR, int MAXJ>
@@ -194,6 +217,25 @@ __global__ void scale_df_kernel(const cdf* __restrict__ w, const df* __restrict_
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x)
     v[e] = cdf_scale(w[e], s[e % R]);
+}
+__global__ void scale_f32_kernel(const c64* __restrict__ w, const float* __restrict__ s, c64* __restrict__ v,
+                                 long long total, int R) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const float f = s[e % R];
+    v[e] = c64{w[e].re * f, w[e].im * f};
+  }
+}
+// v = complex64 (r * s[r]) from a double-float vector (the scaled residual
+// that starts a refinement cycle)
+__global__ void df_to_c64_scaled_kernel(const cdf* __restrict__ r, const double* __restrict__ s, c64* __restrict__ v,
+                                        long long total, int R) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double f = s[e % R];
+    const cdf a = r[e];
+    v[e] = c64{(float)(((double)a.re.h + (double)a.re.l) * f), (float)(((double)a.im.h + (double)a.im.l) * f)};
+  }
 }
 template <typename AR>
 __global__ void to_c64_kernel(const typename AR::V* __restrict__ v, c64* __restrict__ z, long long total) {
@@ -476,7 +518,13 @@ struct Solver {
   // dst = src * f[r]; the host factors are copied synchronously (tiny)
   void scale(const V* src, const std::vector<double>& f, V* dst) {
     note_launch();
-    if constexpr (std::is_same<AR, F64>::value) {
+    if constexpr (std::is_same<AR, F32>::value) {
+      scratch.resize(R);
+      for (int r = 0; r < R; ++r) scratch[r] = (float)f[r];
+      cudaMemcpyAsync(w.s, scratch.data(), R * sizeof(float), cudaMemcpyHostToDevice, s);
+      cudaStreamSynchronize(s);
+      scale_f32_kernel<<<sm_count() * 8, 256, 0, s>>>(src, (const float*)w.s, dst, vs, R);
+    } else if constexpr (std::is_same<AR, F64>::value) {
       cudaMemcpyAsync(w.s, f.data(), R * sizeof(double), cudaMemcpyHostToDevice, s);
       cudaStreamSynchronize(s);
       scale_f64_kernel<<<sm_count() * 8, 256, 0, s>>>(src, (const double*)w.s, dst, vs, R);
@@ -754,6 +802,189 @@ int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs
   return st;
 }
 
+// Mixed-precision refinement (2D, complex64 factors): each cycle restarts
+// from the true residual r = f - A x computed in double-float and runs
+// FGMRES with an FP32 Arnoldi basis (complex64 vectors, FP32 Gram-Schmidt,
+// the products A z_j still in double-float) until its Givens estimate has
+// fallen by inner_tol (or reaches tol ||f||); x is updated in double-float.
+// FP64-class arithmetic is kept exactly where the iterate and the residual
+// that decides convergence are formed.
+int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs_solve_info* info,
+                 cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int R = nrhs;
+  const int m = std::min(std::max(p.opt.restart, 1), 32);
+  const double inner = p.opt.inner_tol;
+  std::lock_guard<std::mutex> guard(pool().mu);
+  KrylovPool& kp = pool();
+  const size_t npts = (size_t)p.npts(), vs = npts * R;
+  const size_t nct = (size_t)sm_count() * 2;
+  const size_t b1 = al256((m + 1) * vs * sizeof(c64)), b2 = al256(m * vs * sizeof(c64)), b3 = al256(vs * sizeof(cdf));
+  const size_t b4 = al256(nct * 33 * R * sizeof(c128)), b5 = al256(34 * R * sizeof(c128)), b6 = al256(R * 16);
+  const size_t need = b1 + b2 + 3 * b3 + b4 + b5 + b6;
+  if (kp.bytes < need) {
+    if (kp.base) cudaFree(kp.base);
+    kp.base = nullptr;
+    kp.bytes = 0;
+    if (cudaMalloc(&kp.base, need) != cudaSuccess) { cudaGetLastError(); return HS_ENOMEM; }
+    kp.bytes = need;
+  }
+  Work w{};
+  char* q = kp.base;
+  w.V = q; q += b1;
+  w.Z = q; q += b2;
+  w.x = q; q += b3;
+  w.f = q; q += b3;
+  cdf* rb = (cdf*)q; q += b3;
+  w.part = (c128*)q; q += b4;
+  w.h = (c128*)q; q += b5;
+  w.s = q;
+  Solver<DF64> K{p, R, (long long)npts, (long long)vs, s, w, sm_count() * 2, {}};
+  Solver<F32> B{p, R, (long long)npts, (long long)vs, s, w, sm_count() * 2, {}};
+  c64* Vb = (c64*)w.V;
+  c64* Z = (c64*)w.Z;
+  cdf* x = (cdf*)w.x;
+  cdf* fi = (cdf*)w.f;
+  K.relayout(f, fi, true);
+  K.relayout(u, x, true);
+  cudaEvent_t ev[4];
+  for (auto& e : ev) cudaEventCreate(&e);
+  double t_apply = 0, t_mv = 0, t_orth = 0;
+  auto elapsed = [](cudaEvent_t a, cudaEvent_t b) { float ms = 0; cudaEventElapsedTime(&ms, a, b); return (double)ms; };
+  std::vector<c128> hbuf(34 * R);
+  auto fetch_h = [&](int rows) {
+    cudaMemcpyAsync(hbuf.data(), w.h, (size_t)rows * R * sizeof(c128), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+  };
+  K.norm2(fi, 0);
+  fetch_h(1);
+  std::vector<double> fn(R), beta0(R);
+  for (int r = 0; r < R; ++r) fn[r] = std::sqrt(hbuf[r].re);
+  std::vector<zc> H((size_t)R * (m + 1) * m), g((size_t)R * (m + 1)), sn((size_t)R * m);
+  std::vector<double> cs((size_t)R * m), relres(R, 1.0), scl(R);
+  std::vector<char> active(R);
+  int it = 0, cycles = 0, applies = 0, st = HS_OK;
+  void* const u_saved = p.d_u;
+  while (true) {
+    K.matvec(x, true, rb, fi);                 // r = f - A x (double-float)
+    K.norm2(rb, 0);
+    fetch_h(1);
+    bool all = true;
+    for (int r = 0; r < R; ++r) {
+      const double beta = std::sqrt(hbuf[r].re);
+      relres[r] = (fn[r] > 0) ? beta / fn[r] : 0.0;
+      active[r] = relres[r] > tol;
+      all = all && !active[r];
+      scl[r] = active[r] ? 1.0 / beta : 0.0;
+      beta0[r] = beta;
+      g[(size_t)r * (m + 1)] = active[r] ? beta : 0.0;
+      for (int k = 1; k <= m; ++k) g[(size_t)r * (m + 1) + k] = 0.0;
+    }
+    if (all || it >= maxit) break;
+    ++cycles;
+    cudaMemcpyAsync(w.s, scl.data(), R * sizeof(double), cudaMemcpyHostToDevice, s);
+    note_launch();
+    df_to_c64_scaled_kernel<<<sm_count() * 8, 256, 0, s>>>(rb, (const double*)w.s, Vb, vs, R);
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      c64* Vj = Vb + (long long)j * vs;
+      c64* W1 = Vb + (long long)(j + 1) * vs;
+      c64* Zj = Z + (long long)j * vs;
+      cudaEventRecord(ev[0], s);
+      cudaMemcpyAsync(Zj, Vj, vs * sizeof(c64), cudaMemcpyDeviceToDevice, s);
+      p.d_u = Zj;
+      st = sweep_internal(p, R, s);
+      p.d_u = u_saved;
+      if (st != HS_OK) break;
+      ++applies;
+      cudaEventRecord(ev[1], s);
+      K.matvec(Zj, false, rb, nullptr);        // A z_j in double-float
+      K.to_c64(rb, W1);
+      cudaEventRecord(ev[2], s);
+      B.dots(Vb, j + 1, W1);                   // FP32 classical Gram-Schmidt
+      B.update(Vb, j + 1, W1, 32);
+      fetch_h(33);
+      std::vector<c128> h1(hbuf.begin(), hbuf.begin() + (size_t)(j + 1) * R);
+      std::vector<double> nw(R), inv(R);
+      for (int r = 0; r < R; ++r) {
+        nw[r] = std::sqrt(hbuf[32 * R + r].re);
+        inv[r] = (active[r] && nw[r] > 0) ? 1.0 / nw[r] : 0.0;
+      }
+      B.scale(W1, inv, W1);
+      cudaEventRecord(ev[3], s);
+      cudaEventSynchronize(ev[3]);
+      t_apply += elapsed(ev[0], ev[1]);
+      t_mv += elapsed(ev[1], ev[2]);
+      t_orth += elapsed(ev[2], ev[3]);
+      bool conv_all = true;
+      for (int r = 0; r < R; ++r) {
+        zc* Hr = &H[(size_t)r * (m + 1) * m];
+        zc* gr = &g[(size_t)r * (m + 1)];
+        double* cr = &cs[(size_t)r * m];
+        zc* sr = &sn[(size_t)r * m];
+        for (int i = 0; i <= j; ++i) Hr[i * m + j] = active[r] ? zc(h1[i * R + r].re, h1[i * R + r].im) : 0.0;
+        Hr[(j + 1) * m + j] = active[r] ? nw[r] : 0.0;
+        for (int i = 0; i < j; ++i) {
+          zc t = cr[i] * Hr[i * m + j] + sr[i] * Hr[(i + 1) * m + j];
+          Hr[(i + 1) * m + j] = -std::conj(sr[i]) * Hr[i * m + j] + cr[i] * Hr[(i + 1) * m + j];
+          Hr[i * m + j] = t;
+        }
+        givens(Hr[j * m + j], Hr[(j + 1) * m + j], cr[j], sr[j]);
+        Hr[j * m + j] = cr[j] * Hr[j * m + j] + sr[j] * Hr[(j + 1) * m + j];
+        Hr[(j + 1) * m + j] = 0.0;
+        gr[j + 1] = -std::conj(sr[j]) * gr[j];
+        gr[j] = cr[j] * gr[j];
+        if (active[r] && std::abs(gr[j + 1]) > std::max(tol * fn[r], inner * beta0[r])) conv_all = false;
+      }
+      ++it;
+      k = j + 1;
+      if (conv_all || it >= maxit) break;
+    }
+    if (st != HS_OK) break;
+    std::vector<c128> y((size_t)k * R);
+    for (int r = 0; r < R; ++r) {
+      zc* Hr = &H[(size_t)r * (m + 1) * m];
+      zc* gr = &g[(size_t)r * (m + 1)];
+      std::vector<zc> yr(k);
+      for (int i = k - 1; i >= 0; --i) {
+        zc acc = active[r] ? gr[i] : 0.0;
+        for (int q2 = i + 1; q2 < k; ++q2) acc -= Hr[i * m + q2] * yr[q2];
+        yr[i] = (active[r] && Hr[i * m + i] != 0.0) ? acc / Hr[i * m + i] : 0.0;
+      }
+      for (int i = 0; i < k; ++i) y[(size_t)i * R + r] = c128{yr[i].real(), yr[i].imag()};
+    }
+    cudaMemcpyAsync(w.h, y.data(), y.size() * sizeof(c128), cudaMemcpyHostToDevice, s);
+    K.xupdate(Z, k, x);
+    cudaStreamSynchronize(s);
+  }
+  p.d_u = u_saved;
+  if (st == HS_OK) K.relayout(x, u, false);
+  cudaError_t e = cudaStreamSynchronize(s);
+  for (auto& q3 : ev) cudaEventDestroy(q3);
+  if (st == HS_OK && e != cudaSuccess) st = cuda_status(e);
+  if (st == HS_OK) {
+    int w3[3];
+    cudaMemcpy(w3, p.d_status, sizeof(w3), cudaMemcpyDeviceToHost);
+    if (w3[0] != HS_OK) st = w3[0];
+  }
+  double mx = 0;
+  bool nan = false;
+  for (int r = 0; r < R; ++r) { mx = std::max(mx, relres[r]); if (!std::isfinite(relres[r])) nan = true; }
+  if (info) {
+    info->iterations = it;
+    info->restarts = cycles;
+    info->applies = applies;
+    info->max_relres = mx;
+    info->t_apply_ms = t_apply;
+    info->t_matvec_ms = t_mv;
+    info->t_orth_ms = t_orth;
+    info->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    info->cnn_applies = 0;
+  }
+  if (st == HS_OK && (mx > tol || nan)) st = HS_ENOCONV;
+  return st;
+}
+
 }  // namespace
 }  // namespace hs
 
@@ -766,6 +997,8 @@ extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double 
   if (nrhs < 1 || nrhs > p.max_nrhs) return HS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   // 3D plans keep the Krylov vectors in FP64 (the double-float kernels are 2D)
+  if (p.prec == HS_C64 && p.dim == 2 && p.opt.krylov_basis == 1 && !p.cnn)
+    return solve_refine(p, f, u, nrhs, tol, maxit, info, s);
   return (p.prec == HS_C64 && p.dim == 2) ? solve_t<DF64>(p, f, u, nrhs, tol, maxit, info, s)
                                           : solve_t<F64>(p, f, u, nrhs, tol, maxit, info, s);
 }

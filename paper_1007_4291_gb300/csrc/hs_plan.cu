@@ -119,6 +119,8 @@ extern "C" int hs_default_options(hs_options* opt) {
   opt->spin_budget = 1LL << 30;
   opt->graphs = 1;
   opt->frontal_gemm = 3;
+  opt->krylov_basis = 1;
+  opt->inner_tol = 1e-4;
   opt->tune_cache = nullptr;
   return HS_OK;
 }
@@ -258,6 +260,8 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
       opt.max_nrhs > 4096 || opt.restart < 1 || opt.chunk < 0 || opt.chunk == 1 || opt.spin_budget < 1)
     return HS_EINVAL;
   if (opt.factor_prec != HS_C64 && opt.factor_prec != HS_C128) return HS_EINVAL;
+  if ((opt.krylov_basis != 0 && opt.krylov_basis != 1) || !(opt.inner_tol > 0.0 && opt.inner_tol < 1.0))
+    return HS_EINVAL;
   for (long long k = 0; k < (long long)n * n; ++k)
     if (!(c[k] > 0.0) || !std::isfinite(c[k])) return HS_EINVAL;
 

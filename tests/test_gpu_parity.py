@@ -214,3 +214,30 @@ def test_solve_with_c64_factors_reaches_fp64_class_tolerance():
             assert res <= 1e-10, res
     finally:
         hs.hs_destroy(plan)
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_refinement_mode_reaches_tolerance(tol):
+    """FP32-basis FGMRES cycles restarted from the double-float residual
+    (krylov_basis = 1) reach FP64-class tolerances under the oracle's operator."""
+    n, bp = 63, 8
+    c = I.random_velocity(n, 2)
+    omega = 2 * np.pi * 4.0
+    R = 3
+    o = hs.hs_default_options(alpha=2.0, pml_C=C_PML, layers_per_step=1, chunk=16, max_nrhs=R, restart=20,
+                              krylov_basis=1, inner_tol=1e-5)
+    plan = hs.hs_setup(c.ravel(), omega, n, 2, bp, bp, o)
+    try:
+        f = I.point_sources(n, R, 1, bp)
+        fg = gpu(f)
+        ug = torch.zeros_like(fg)
+        code, info = hs.hs_solve(plan, fg, ug, R, tol, 300)
+        assert code == hs.HS_OK, info
+        A0 = H.helmholtz_matrix(c, omega, bp, C_PML, 0.0)
+        u = ug.cpu().numpy()
+        for k in range(R):
+            res = np.linalg.norm(f[k].ravel() - A0 @ u[k].ravel()) / np.linalg.norm(f[k].ravel())
+            assert res <= tol, res
+        print("refinement to %g: %d iterations in %d cycles" % (tol, info["iterations"], info["restarts"]))
+    finally:
+        hs.hs_destroy(plan)
