@@ -60,13 +60,19 @@ def parse():
     return ap.parse_args()
 
 
-def workload(args):
+def source_seed(rank):
+    """Point-source seed of a rank's batch: rank 0 solves the headline batch
+    (seed 1); the other replicas solve independent batches."""
+    return 1 + 1000 * rank
+
+
+def workload(args, rank=0):
     from paper_1007_4291_gb300 import inputs as I
     n = args.n
     bp = b = 12
     freq = (n + 1) / 16.0          # 16 points per wavelength at c = 1
     c = I.random_velocity(n, 0)    # smooth random field in [0.8, 1.2]
-    f = I.point_sources(n, args.nrhs, 1, bp)
+    f = I.point_sources(n, args.nrhs, source_seed(rank), bp)
     return dict(n=n, bp=bp, b=b, omega=2 * np.pi * freq, freq=freq, alpha=2.0, C=20.0, c=c, f=f)
 
 
@@ -349,6 +355,18 @@ def three_d(stream, n=63, nrhs=16):
     return out
 
 
+def aggregate(ms_local, world, nrhs, dist=None, device="cpu"):
+    """Whole-job figures of a replica run: the slowest rank's time per step
+    (MAX over ranks) and the RHS solved per second by all ranks together."""
+    import torch
+    ms_all = ms_local
+    if dist is not None:
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    return ms_all, world * nrhs / (ms_all / 1e3)
+
+
 def run_ours(args):
     import torch
     import __graft_entry__ as G
@@ -366,7 +384,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     G.build()
     lib = hs.load()
-    wl = workload(args)
+    wl = workload(args, rank)
     n, R = wl["n"], args.nrhs
     opt = hs.hs_default_options(alpha=wl["alpha"], pml_C=wl["C"], layers_per_step=args.dl, factor_prec=args.prec,
                                 chunk=args.chunk, max_nrhs=R, restart=args.restart, krylov_basis=args.krylov_basis)
@@ -406,12 +424,7 @@ def run_ours(args):
     clocks = sampler.stop()
     launches = lib.hs_kernel_launches() - l0
     ms = e0.elapsed_time(e1) / args.steps
-    ms_all = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = float(t.item())
-    value = world * R / (ms_all / 1e3)
+    ms_all, value = aggregate(ms, world, R, dist, "cuda")
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -434,12 +447,9 @@ def run_ours(args):
         for _ in range(args.steps):
             step_e2e()
         barrier()
-        we = (time.perf_counter() - t0) / args.steps
-        if dist is not None:
-            t = torch.tensor([we], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            we = float(t.item())
-        e2e = {"value": world * R / we, "unit": UNIT, "h2d_bytes_per_step": int(wl["f"].nbytes + c_host.nbytes),
+        we_ms, e2e_value = aggregate((time.perf_counter() - t0) / args.steps * 1e3, world, R, dist, "cuda")
+        we = we_ms / 1e3
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(wl["f"].nbytes + c_host.nbytes),
                "d2h_bytes_per_step": int(wl["f"].nbytes), "ms_per_step": we * 1e3}
 
     # roofline of the dominant kernel: the sweep application (FP32 ALU bound at 64 RHS)
