@@ -30,21 +30,24 @@ constexpr int TNC = 32;        // tile columns, complex
 constexpr int TN = 2 * TNC;    // MMA N (real)
 constexpr int KC = 16;         // complex K per chunk
 constexpr int KR = 2 * KC;     // real K per chunk
-constexpr uint32_t A_BYTES = TM * KR * 4;   // 16 KB
-constexpr uint32_t B_BYTES = TN * KR * 4;   //  8 KB
-constexpr uint32_t A_LBO = TM * 16, B_LBO = TN * 16;
+// K-adjacent core matrices are LBO bytes apart: one 16-byte pad after each
+// k-group of rows keeps the 16-byte stores of 8 consecutive k-groups in
+// distinct banks.
+constexpr uint32_t A_LBO = TM * 16 + 16, B_LBO = TN * 16 + 16;
+constexpr uint32_t A_BYTES = (KR / 4) * A_LBO;   // 16.1 KB
+constexpr uint32_t B_BYTES = (KR / 4) * B_LBO;   //  8.1 KB
 constexpr uint32_t IDESC = tc_idesc(2u, TM, TN);    // TF32 A and B, FP32 accumulator
-// Requested shared memory: the two precision halves of A and B plus the
-// barrier; generous so that every address a descriptor forms stays inside.
-constexpr uint32_t SMEM_BYTES = 96 * 1024;
+// Shared memory: the two precision halves of A and B plus the barrier.
+constexpr uint32_t SMEM_BYTES = 2 * A_BYTES + 2 * B_BYTES + 16;
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-__device__ __forceinline__ void put(float* buf, int rows, int r, int k, float v) {
-  buf[((k >> 2) * rows + r) * 4 + (k & 3)] = v;
+// element (row r, real k) of a [k/4][rows][4] operand with row groups lbo bytes apart
+__device__ __forceinline__ void put(float* buf, uint32_t lbo, int r, int k, float v) {
+  buf[(k >> 2) * (lbo / 4) + r * 4 + (k & 3)] = v;
 }
 
-__global__ void __launch_bounds__(128, 1) zgemm_tf32_kernel(const TcGemmJob* jobs, const TcGemmTile* tiles, int split,
+__global__ void __launch_bounds__(128, 4) zgemm_tf32_kernel(const TcGemmJob* jobs, const TcGemmTile* tiles, int split,
                                                            int* status, long long spin) {
   extern __shared__ __align__(1024) unsigned char sm[];
   float* Ah = reinterpret_cast<float*>(sm);
@@ -76,22 +79,27 @@ __global__ void __launch_bounds__(128, 1) zgemm_tf32_kernel(const TcGemmJob* job
   const int nchunks = (jb.K + KC - 1) / KC;
   for (int ch = 0; ch < nchunks; ++ch) {
     const int k0 = ch * KC;
-    // A chunk: row r = tid, 16 complex values
-    {
-      const int m = m0 + tid;
-#pragma unroll 4
-      for (int kk = 0; kk < KC; ++kk) {
-        const int k = k0 + kk;
-        c64 v{0.f, 0.f};
-        if (m < jb.M && k < jb.K) v = A[(long long)m * jb.lda + k];
-        const float hr = split ? tf32_hi(v.re) : v.re, hi_ = split ? tf32_hi(v.im) : v.im;
-        put(Ah, TM, tid, 2 * kk, hr);
-        put(Ah, TM, tid, 2 * kk + 1, hi_);
-        if (split) {
-          put(Al, TM, tid, 2 * kk, v.re - hr);
-          put(Al, TM, tid, 2 * kk + 1, v.im - hi_);
-        }
+    // A chunk: 128 rows x 8 k-groups of 2 complex (16 bytes); consecutive
+    // threads read consecutive 16-byte pieces of one row (coalesced)
+    for (int e = tid; e < TM * (KC / 2); e += blockDim.x) {
+      const int row = e / (KC / 2), kg = e % (KC / 2);
+      const int m = m0 + row, k = k0 + 2 * kg;
+      c64 v0{0.f, 0.f}, v1{0.f, 0.f};
+      if (m < jb.M) {
+        const c64* ar = A + (long long)m * jb.lda;
+        if (k < jb.K) v0 = ar[k];
+        if (k + 1 < jb.K) v1 = ar[k + 1];
       }
+      const float x[4] = {v0.re, v0.im, v1.re, v1.im};
+      float hx[4], lx[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        hx[q] = split ? tf32_hi(x[q]) : x[q];
+        lx[q] = x[q] - hx[q];
+      }
+      *reinterpret_cast<float4*>(Ah + kg * (A_LBO / 4) + row * 4) = make_float4(hx[0], hx[1], hx[2], hx[3]);
+      if (split)
+        *reinterpret_cast<float4*>(Al + kg * (A_LBO / 4) + row * 4) = make_float4(lx[0], lx[1], lx[2], lx[3]);
     }
     // Bt chunk: (k, n) pairs of the chunk, 4 per thread
     for (int e = tid; e < KC * TNC; e += blockDim.x) {
@@ -105,8 +113,8 @@ __global__ void __launch_bounds__(128, 1) zgemm_tf32_kernel(const TcGemmJob* job
         const int row = 2 * nn + (q >> 1), col = 2 * kk + (q & 1);
         const float x = vals[q];
         const float h = split ? tf32_hi(x) : x;
-        put(Bh, TN, row, col, h);
-        if (split) put(Bl, TN, row, col, x - h);
+        put(Bh, B_LBO, row, col, h);
+        if (split) put(Bl, B_LBO, row, col, x - h);
       }
     }
     fence_proxy_async_smem();

@@ -34,9 +34,11 @@ constexpr int NC = 32;                  // output channels (MMA N)
 constexpr uint32_t B_STEP = 2 * NC * 16;          // bytes of B per K-step
 constexpr uint32_t B_BYTES = KSTEPS * B_STEP;     // 18,432
 constexpr uint32_t TMEM_COLS = 32;
-// Shared memory requested per CTA.  Larger than the tile needs: every operand
-// address a descriptor can form from this layout stays inside the allocation.
-constexpr uint32_t SMEM_BYTES = 160 * 1024;
+// Shared memory per CTA: A tile, B operand, mbarrier, TMEM slot, bias; four
+// CTAs share an SM (each holds 32 TMEM columns) so that one CTA's loads
+// overlap the others' MMAs and epilogues.
+constexpr uint32_t SMEM_BYTES = A_BYTES + B_BYTES + 16 + 32 * 4;
+constexpr int CTAS_PER_SM = 4;
 
 constexpr uint32_t IDESC = tc_idesc(1u, TM, NC);   // bf16 A and B, FP32 accumulator
 
@@ -54,7 +56,7 @@ __global__ void pack_w2_kernel(const float* __restrict__ wq, uint4* __restrict__
   out[i] = *reinterpret_cast<const uint4*>(v);
 }
 
-__global__ void __launch_bounds__(128, 1) conv2_tc_kernel(const __nv_bfloat16* __restrict__ x, int n, int R,
+__global__ void __launch_bounds__(128, CTAS_PER_SM) conv2_tc_kernel(const __nv_bfloat16* __restrict__ x, int n, int R,
                                                         const uint4* __restrict__ wpk, const float* __restrict__ wq,
                                                         __nv_bfloat16* __restrict__ y, int* status, long long spin) {
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -162,7 +164,7 @@ int conv2_tc(Cnn& c, int R, int n, cudaStream_t s) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long ntiles = (long long)R * n * ((n + TM - 1) / TM);
-  const int grid = (int)std::min<long long>(ntiles, (long long)sms);
+  const int grid = (int)std::min<long long>(ntiles, (long long)sms * CTAS_PER_SM);
   note_launch();
   conv2_tc_kernel<<<grid, 128, SMEM_BYTES, s>>>(c.h1, n, R, reinterpret_cast<const uint4*>(c.w2tc), c.wq, c.h2,
                                                 c.status, 1LL << 30);

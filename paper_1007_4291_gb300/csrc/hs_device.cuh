@@ -124,8 +124,12 @@ __host__ __device__ __forceinline__ long long payload_elems(int W, int d_out) {
   long long e = (long long)(W + d_out) * payload_ld(W) + W;
   return (e + 1) & ~1LL;
 }
-// Reduced-system factors per separator: Gamma and F, each W x (W+2).
-__host__ __device__ __forceinline__ long long red_elems(int W) { return 2LL * W * payload_ld(W); }
+// Reduced-system factors per separator, each W x (W+2): Gamma, F, and (at the
+// twist separator only) the bottom coupling F'.
+__host__ __device__ __forceinline__ long long red_elems(int W) { return 3LL * W * payload_ld(W); }
+// Twist separator of a chain of K separators: the top and bottom halves of the
+// reduced system are eliminated toward it from both ends.
+__host__ __device__ __forceinline__ int twist_index(int K) { return K / 2; }
 // Corner blocks per interior chunk: G_r, W_l, W_r, each W x (W+1) (setup only).
 __host__ __device__ __forceinline__ long long cor_elems(int W) { return 3LL * W * (W + 1); }
 

@@ -276,11 +276,16 @@ __device__ __forceinline__ void chunk_item(const FactorArgs& a, const int bi, co
   }
 }
 
-// Block LU of the reduced (separator) system of each block:
-//   Sigma_kk   = D_s - C_{s-1} G^{(k)}_r C_{s-1} - C_s W^{(k+1)}_l C_s
-//   Sigma_k,k-1 = -C_{s-1} W^{(k)}_r C_{s'}        (s' = previous separator)
-//   F_k = Sigma_k,k-1 Gamma_{k-1},  Gamma_k = (Sigma_kk - F_k Sigma_k,k-1^t)^{-1}
-// Reduced (separator) system of block bi.
+// Twisted block LU of the reduced (separator) system of each block: the
+// separators s_0..s_{K-1} form a block-tridiagonal system with
+//   Sigma_kk     = D_s - C_{s-1} G^{(k)}_r C_{s-1} - C_s W^{(k+1)}_l C_s
+//   Sigma_k,k-1  = -C_{s-1} W^{(k)}_r C_{s'}        (s' = previous separator)
+// eliminated from both ends toward the twist m = K/2:
+//   top    (k < m):  F_k = Sigma_k,k-1 Gamma_{k-1},   Gamma_k  = (Sigma_kk - F_k Sigma_k,k-1^t)^{-1}
+//   bottom (k > m):  F'_k = Sigma_k+1,k^t Gamma'_{k+1}, Gamma'_k = (Sigma_kk - F'_k Sigma_k+1,k)^{-1}
+//   twist:           Gamma_m = (Sigma_mm - F_m Sigma_m,m-1^t - F'_m Sigma_m+1,m)^{-1}
+// Slot k stores [Gamma_k or Gamma'_k | F_k or F'_k | F'_m at the twist].  The
+// two chains of the separator solve are then half as long.
 template <typename R, int W>
 __device__ __forceinline__ void reduced_item(const FactorArgs& a, const int bi) {
   using C = cplx<R>;
@@ -295,81 +300,129 @@ __device__ __forceinline__ void reduced_item(const FactorArgs& a, const int bi) 
   c128* s2 = reinterpret_cast<c128*>(cv + 2 * W);
   int* piv = reinterpret_cast<int*>(s2 + 3 * 32);
   const int lane = threadIdx.x;
-  C* facb = reinterpret_cast<C*>(a.fac);
   C* corb = reinterpret_cast<C*>(a.cor);
   C* redb = reinterpret_cast<C*>(a.red);
-  {
-    const BlockDesc d = a.blocks[bi];
-    (void)facb;
-    for (int t = lane; t < 3 * d.w; t += 32) s2[t] = a.s2win[d.s2_off + t];
+  const BlockDesc d = a.blocks[bi];
+  for (int t = lane; t < 3 * d.w; t += 32) s2[t] = a.s2win[d.s2_off + t];
+  __syncwarp();
+  const int K = a.P - 1, m = twist_index(K);
+  auto sep_col = [&](int k) { return (k + 1) * a.L - 1; };
+  auto slot = [&](int k) { return redb + d.red_off + (long long)k * red_elems(W); };
+  // A = Sigma_kk
+  auto build_diag = [&](C* A, int k) {
+    const int s = sep_col(k);
+    const C* corL = corb + d.cor_off + (long long)k * cor_elems(W);        // interior k (left)
+    const C* corR = corb + d.cor_off + (long long)(k + 1) * cor_elems(W);  // interior k+1 (right)
+    build_d<R, W>(a, d, s2, s, A, lane);
+    if (lane < W) cv[lane] = coupling<R>(a, d, s2, s - 1, lane);
+    if (lane < W) cv[W + lane] = coupling<R>(a, d, s2, s, lane);
     __syncwarp();
-    C *A = bufA, *Gam = bufG, *Sig = bufS, *F = bufF;
-    bool ok = true;
-    for (int k = 0; k + 1 < a.P; ++k) {
-      const int s = (k + 1) * a.L - 1;
-      const C* corL = corb + d.cor_off + (long long)k * cor_elems(W);        // interior k (left)
-      const C* corR = corb + d.cor_off + (long long)(k + 1) * cor_elems(W);  // interior k+1 (right)
-      C* red = redb + d.red_off + (long long)k * red_elems(W);
-      build_d<R, W>(a, d, s2, s, A, lane);
-      // - C_{s-1} Gr_k C_{s-1}
-      if (lane < W) cv[lane] = coupling<R>(a, d, s2, s - 1, lane);
-      if (lane < W) cv[W + lane] = coupling<R>(a, d, s2, s, lane);
-      __syncwarp();
-      if (lane < W) {
-        const C cp = cv[lane], cq = cv[W + lane];
-        for (int q = 0; q < W; ++q) {
-          C t1 = cmul(cmul(cp, corL[lane * LD + q]), cv[q]);
-          C t2 = cmul(cmul(cq, corR[(long long)W * LD + lane * LD + q]), cv[W + q]);
-          A[lane * LD + q] = csub(csub(A[lane * LD + q], t1), t2);
-        }
+    if (lane < W) {
+      const C cp = cv[lane], cq = cv[W + lane];
+      for (int q = 0; q < W; ++q) {
+        C t1 = cmul(cmul(cp, corL[lane * LD + q]), cv[q]);
+        C t2 = cmul(cmul(cq, corR[(long long)W * LD + lane * LD + q]), cv[W + q]);
+        A[lane * LD + q] = csub(csub(A[lane * LD + q], t1), t2);
       }
-      __syncwarp();
-      if (k >= 1) {
-        const int sp = k * a.L - 1;
-        // Sig[p][q] = -c_{s-1}[p] Wr_k[p][q] c_{sp}[q]
-        if (lane < W) cv[W + lane] = coupling<R>(a, d, s2, sp, lane);
-        __syncwarp();
-        if (lane < W) {
-          const C cp = cv[lane];
-          for (int q = 0; q < W; ++q) {
-            C t = cmul(cmul(cp, corL[2LL * W * LD + lane * LD + q]), cv[W + q]);
-            Sig[lane * LD + q] = C{-t.re, -t.im};
-          }
-        }
-        __syncwarp();
-        // F = Sig * Gam_prev
-        C acc[W];
-#pragma unroll
-        for (int q = 0; q < W; ++q) acc[q] = C{0, 0};
-        if (lane < W) {
-          for (int q = 0; q < W; ++q) {
-            C t = Sig[lane * LD + q];
-#pragma unroll
-            for (int qq = 0; qq < W; ++qq) cfma(acc[qq], t, Gam[q * LD + qq]);
-          }
-#pragma unroll
-          for (int q = 0; q < W; ++q) F[lane * LD + q] = acc[q];
-        }
-        __syncwarp();
-        // A -= F Sig^t
-        if (lane < W) {
-          for (int q = 0; q < W; ++q) {
-            C t{0, 0};
-            for (int u = 0; u < W; ++u) cfma(t, F[lane * LD + u], Sig[q * LD + u]);
-            A[lane * LD + q] = csub(A[lane * LD + q], t);
-          }
-        }
-        __syncwarp();
-        store_rows<R, W>(red + (long long)W * LDP, F, lane, 0, W, LDP);
+    }
+    __syncwarp();
+  };
+  // Sig = Sigma_{k,k-1} (k >= 1): -c_{s-1}[p] Wr_k[p][q] c_{s'}[q]
+  auto build_sub = [&](C* Sig, int k) {
+    const int s = sep_col(k), sp = sep_col(k - 1);
+    const C* corL = corb + d.cor_off + (long long)k * cor_elems(W);
+    if (lane < W) cv[lane] = coupling<R>(a, d, s2, s - 1, lane);
+    if (lane < W) cv[W + lane] = coupling<R>(a, d, s2, sp, lane);
+    __syncwarp();
+    if (lane < W) {
+      const C cp = cv[lane];
+      for (int q = 0; q < W; ++q) {
+        C t = cmul(cmul(cp, corL[2LL * W * LD + lane * LD + q]), cv[W + q]);
+        Sig[lane * LD + q] = C{-t.re, -t.im};
       }
+    }
+    __syncwarp();
+  };
+  // F = op(Sig) Gam, op = identity (top) or transpose (bottom)
+  auto mul_sg = [&](C* F, const C* Sig, const C* Gam, bool trans) {
+    C acc[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) acc[q] = C{0, 0};
+    if (lane < W) {
+      for (int u = 0; u < W; ++u) {
+        const C t = trans ? Sig[u * LD + lane] : Sig[lane * LD + u];
+#pragma unroll
+        for (int qq = 0; qq < W; ++qq) cfma(acc[qq], t, Gam[u * LD + qq]);
+      }
+#pragma unroll
+      for (int q = 0; q < W; ++q) F[lane * LD + q] = acc[q];
+    }
+    __syncwarp();
+  };
+  // A -= F op(Sig): op = transpose (top: Sigma_k,k-1^t) or identity (bottom: Sigma_k+1,k)
+  auto sub_fs = [&](C* A, const C* F, const C* Sig, bool trans) {
+    if (lane < W) {
+      for (int q = 0; q < W; ++q) {
+        C t{0, 0};
+        for (int u = 0; u < W; ++u) cfma(t, F[lane * LD + u], trans ? Sig[q * LD + u] : Sig[u * LD + q]);
+        A[lane * LD + q] = csub(A[lane * LD + q], t);
+      }
+    }
+    __syncwarp();
+  };
+  C *A = bufA, *Gam = bufG, *Sig = bufS, *F = bufF;
+  bool ok = true;
+  // top chain k = 0 .. m (the twist gets its top coupling but is not inverted yet)
+  for (int k = 0; k <= m; ++k) {
+    build_diag(A, k);
+    if (k >= 1) {
+      build_sub(Sig, k);
+      mul_sg(F, Sig, Gam, false);
+      sub_fs(A, F, Sig, true);
+      store_rows<R, W>(slot(k) + (long long)W * LDP, F, lane, 0, W, LDP);
+    }
+    if (k < m) {
       ok &= invert_inplace<R, W>(A, piv, lane);
-      store_rows<R, W>(red, A, lane, 0, W, LDP);
+      store_rows<R, W>(slot(k), A, lane, 0, W, LDP);
       C* t = A; A = Gam; Gam = t;
       __syncwarp();
     }
-    if (!ok && lane == 0) set_status(a.status, HS_EBREAKDOWN, bi, -1);
+  }
+  // park Sigma_mm - F_m Sigma_m,m-1^t in the twist's Gamma slot
+  store_rows<R, W>(slot(m), A, lane, 0, W, LDP);
+  __syncwarp();
+  // bottom chain k = K-1 .. m+1
+  for (int k = K - 1; k > m; --k) {
+    build_diag(A, k);
+    if (k < K - 1) {
+      build_sub(Sig, k + 1);
+      mul_sg(F, Sig, Gam, true);
+      sub_fs(A, F, Sig, false);
+      store_rows<R, W>(slot(k) + (long long)W * LDP, F, lane, 0, W, LDP);
+    }
+    ok &= invert_inplace<R, W>(A, piv, lane);
+    store_rows<R, W>(slot(k), A, lane, 0, W, LDP);
+    C* t = A; A = Gam; Gam = t;
     __syncwarp();
   }
+  // twist: Gamma_m = (parked - F'_m Sigma_m+1,m)^{-1}
+  {
+    const C* parked = slot(m);
+    if (lane < W)
+      for (int q = 0; q < W; ++q) A[lane * LD + q] = parked[lane * LDP + q];
+    __syncwarp();
+    if (m < K - 1) {
+      build_sub(Sig, m + 1);
+      mul_sg(F, Sig, Gam, true);
+      sub_fs(A, F, Sig, false);
+      store_rows<R, W>(slot(m) + 2LL * W * LDP, F, lane, 0, W, LDP);
+    }
+    ok &= invert_inplace<R, W>(A, piv, lane);
+    store_rows<R, W>(slot(m), A, lane, 0, W, LDP);
+    __syncwarp();
+  }
+  if (!ok && lane == 0) set_status(a.status, HS_EBREAKDOWN, bi, -1);
+  __syncwarp();
 }
 
 // One work item of the batched setup: a chunk of a block of a problem.

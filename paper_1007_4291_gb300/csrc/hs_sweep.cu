@@ -442,61 +442,90 @@ __global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase1_kernel(SweepA
 }
 
 // ---------------------------------------------------------------- phase 2
-// Block LU solve of the separator system, one warp per RHS (lane p = row p),
-// warps independent.  rho_k = -(rc_k + lc_{k+1}) of every separator is
-// gathered into shared memory first (two independent loads per value); the
-// forward chain psi_k = rho_k - F_k psi_{k-1} keeps psi_k there, and the
-// backward chain x_k = Gamma_k psi_k - F_{k+1}^t x_{k+1} reads it back.  The
-// chain variable is exchanged through shared memory (broadcast loads).  A
-// producer warp streams (Gamma_k | F_k) through an S2-deep TMA ring (forward
-// order, then backward order).
-constexpr int WPC = NT / 32;  // RHS (consumer warps) per CTA in phase 2
-constexpr int S2 = 4;         // TMA ring depth of phase 2
+// Twisted block LU solve of the separator system (see the setup): for each
+// RHS a top warp and a bottom warp run the two half chains at once,
+//   top     psi_k  = rho_k - F_k psi_{k-1}            k = 0 .. m-1
+//   bottom  psi'_k = rho_k - F'_k psi'_{k+1}          k = K-1 .. m+1
+//   twist   x_m = Gamma_m (rho_m - F_m psi_{m-1} - F'_m psi'_{m+1})
+//   top     x_k = Gamma_k psi_k - F_{k+1}^t x_{k+1}    k = m-1 .. 0
+//   bottom  x_k = Gamma'_k psi'_k - F'_{k-1}^t x_{k-1} k = m+1 .. K-1
+// (lane p = row p).  rho_k = -(rc_k + lc_{k+1}) is gathered into shared
+// memory first; the chain variables are exchanged there (broadcast loads).
+// The two warps of a RHS meet twice on a named barrier (psi'_{m+1}, then
+// x_m); each half has its own producer warp streaming the separator factors
+// through an S2-deep TMA ring in the order its chain uses them.
+constexpr int WPC = 4;           // RHS per CTA in phase 2
+constexpr int NC2 = 2 * WPC;     // consumer warps (top and bottom per RHS)
+// TMA ring depth: 4 stages per half, 2 when the separator factors are large
+template <typename R, int W> struct Ring2 {
+  static constexpr int S = (8LL * 3 * W * (W + 2) * 2 * (long long)sizeof(R) <= 128 * 1024) ? 4 : 2;
+};
 
 template <typename R, int W>
 size_t phase2_smem(int nsep) {
-  return 256 + (size_t)S2 * round128((size_t)red_elems(W) * sizeof(cplx<R>)) +
-         (size_t)WPC * (nsep + 1) * W * sizeof(cplx<R>);
+  return 256 + (size_t)2 * Ring2<R, W>::S * round128((size_t)red_elems(W) * sizeof(cplx<R>)) +
+         (size_t)WPC * (nsep + 3) * W * sizeof(cplx<R>);
+}
+
+// Named barrier of the two warps of one RHS, returning the AND of `v`.
+__device__ __forceinline__ bool pair_barrier_and(int id, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, 64, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id)
+      : "memory");
+  return r != 0;
 }
 
 template <typename R, int W>
-__global__ void __launch_bounds__(NT + 32) phase2_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(NC2 * 32 + 64) phase2_kernel(SweepArgs a) {
   using C = cplx<R>;
   constexpr int LDP = W + 2;
+  constexpr int S2 = Ring2<R, W>::S;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
-  uint64_t* empty = full + S2;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);     // [2][S2]
+  uint64_t* empty = full + 2 * S2;                            // [2][S2]
   const int front = blockIdx.z;
   const BlockDesc& d = a.blk[front];
   const long long re = red_elems(W);
   const uint32_t rbytes = (uint32_t)(re * sizeof(C));
   const size_t sstride = round128(rbytes);
-  const int nsep = a.P - 1;
-  const int nuses = 2 * nsep;
-  C* rz = reinterpret_cast<C*>(smem_raw + 256 + (size_t)S2 * sstride);
+  const int K = a.P - 1, m = twist_index(K), nb = K - 1 - m;
+  const int nuse[2] = {2 * m + 1, nb > 0 ? 2 * nb + 1 : 0};
+  C* rz = reinterpret_cast<C*>(smem_raw + 256 + (size_t)2 * S2 * sstride);
   const C* red = reinterpret_cast<const C*>(a.red) + d.red_off;
   const int tid = threadIdx.x;
-  auto stage = [&](int u) { return reinterpret_cast<C*>(smem_raw + 256 + (size_t)(u % S2) * sstride); };
-  auto sep_of_use = [&](int u) { return (u < nsep) ? u : (nuses - 1 - u); };
+  auto stage = [&](int h, int u) { return reinterpret_cast<C*>(smem_raw + 256 + (size_t)(h * S2 + u % S2) * sstride); };
+  // separator of use u of half h
+  auto slot_of = [&](int h, int u) {
+    if (h == 0) return u <= m ? u : 2 * m - u;              // 0..m-1, m, m-1..0
+    return u < nb ? K - 1 - u : m + (u - nb);               // K-1..m+1, m..K-1
+  };
 
   if (tid == 0) {
-    for (int u = 0; u < S2; ++u) {
+    for (int u = 0; u < 2 * S2; ++u) {
       mbar_init(&full[u], 1);
       mbar_init(&empty[u], WPC);
     }
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid >= NT) {
-    if (tid == NT)
-      ring_producer(full, empty, S2, nuses, a.spin, a.status, front, [&](int t) {
-        mbar_arrive_expect_tx(&full[t % S2], rbytes);
-        tma_bulk_g2s(stage(t), red + (long long)sep_of_use(t) * re, rbytes, &full[t % S2]);
+  if (tid >= NC2 * 32) {
+    const int h = (tid - NC2 * 32) >> 5;
+    if ((tid & 31) == 0 && nuse[h] > 0)
+      ring_producer(full + h * S2, empty + h * S2, S2, nuse[h], a.spin, a.status, front, [&](int t) {
+        mbar_arrive_expect_tx(&full[h * S2 + t % S2], rbytes);
+        tma_bulk_g2s(stage(h, t), red + (long long)slot_of(h, t) * re, rbytes, &full[h * S2 + t % S2]);
       });
     return;
   }
   const int lane = tid & 31, wq = tid >> 5;
-  const int r = blockIdx.y * WPC + wq;
+  const int rhs = wq & (WPC - 1), half = wq / WPC;
+  const int r = blockIdx.y * WPC + rhs;
   const bool valid = r < a.R;
   const int rr = valid ? r : (a.R - 1);
   const int pl = lane < W ? lane : 0;
@@ -504,80 +533,167 @@ __global__ void __launch_bounds__(NT + 32) phase2_kernel(SweepArgs a) {
   const C* lcb = reinterpret_cast<const C*>(a.lc);
   C* xsb = reinterpret_cast<C*>(a.xs);
   const long long fb = (long long)front * a.P;
-  C* myrz = rz + (size_t)wq * (nsep + 1) * W;   // nsep psi vectors + one exchange slot
-  C* xch = myrz + (size_t)nsep * W;
-  // rho_k for every separator (all loads issued before any use)
-  for (int k0 = 0; k0 < nsep; k0 += 16) {
+  C* myrz = rz + (size_t)rhs * (K + 3) * W;    // [0..K-1] rho/psi, [K] x_m, [K+1+half] own exchange
+  C* xm = myrz + (size_t)K * W;
+  C* xch = myrz + (size_t)(K + 1 + half) * W;
+  uint64_t* fl = full + half * S2;
+  uint64_t* em = empty + half * S2;
+  // rho_k of this half's separators (top: 0..m, bottom: m+1..K-1)
+  const int k_lo = half == 0 ? 0 : m + 1, k_hi = half == 0 ? m + 1 : K;
+  for (int k0 = k_lo; k0 < k_hi; k0 += 16) {
     C v1[16], v2[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int k = min(k0 + q, nsep - 1);
+      const int k = min(k0 + q, k_hi - 1);
       v1[q] = rcb[((fb + k) * a.R + rr) * W + pl];
       v2[q] = lcb[((fb + k + 1) * a.R + rr) * W + pl];
     }
 #pragma unroll
     for (int q = 0; q < 16; ++q)
-      if (k0 + q < nsep && lane < W) myrz[(k0 + q) * W + lane] = C{-(v1[q].re + v2[q].re), -(v1[q].im + v2[q].im)};
+      if (k0 + q < k_hi && lane < W) myrz[(k0 + q) * W + lane] = C{-(v1[q].re + v2[q].re), -(v1[q].im + v2[q].im)};
   }
   __syncwarp();
   bool ok = true;
   int t = 0;
-  for (int k = 0; k < nsep; ++k, ++t) {
-    const C* F = stage(t) + W * LDP;
-    ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[t % S2], (t / S2) & 1, a.spin));
-    if (!ok) break;
-    C s0 = myrz[k * W + pl], s1{0, 0}, s2{0, 0}, s3{0, 0};
-    if (k > 0) {
-      const C* fr = F + pl * LDP;
-      const C* pv = myrz + (k - 1) * W;     // psi_{k-1}, read by every lane
-#pragma unroll
-      for (int q = 0; q < W; q += 4) {
-        cfms(s0, fr[q], pv[q]);
-        cfms(s1, fr[q + 1], pv[q + 1]);
-        cfms(s2, fr[q + 2], pv[q + 2]);
-        cfms(s3, fr[q + 3], pv[q + 3]);
-      }
-    }
-    const C psi = cadd(cadd(s0, s1), cadd(s2, s3));
-    __syncwarp();
-    if (lane < W) myrz[k * W + lane] = psi;
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[t % S2]);
-  }
-  C fcol[W];
-  for (int k = nsep - 1; k >= 0 && ok; --k, ++t) {
-    const C* Gm = stage(t);
-    const C* F = Gm + W * LDP;
-    ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[t % S2], (t / S2) & 1, a.spin));
-    if (!ok) break;
-    // Gamma_k psi_k: Gamma_k is symmetric, so lane p reads column p (no
-    // bank conflicts); psi_k is read by every lane
-    const C* ps = myrz + k * W;
-    C s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
+  // y = v - Mrow * prev with Mrow the row pl of a W x W block (row stride LDP)
+  auto row_apply = [&](C v, const C* Mrow, const C* prev) {
+    C s1{0, 0}, s2{0, 0}, s3{0, 0};
 #pragma unroll
     for (int q = 0; q < W; q += 4) {
-      cfma(s0, Gm[q * LDP + pl], ps[q]);
-      cfma(s1, Gm[(q + 1) * LDP + pl], ps[q + 1]);
-      cfma(s2, Gm[(q + 2) * LDP + pl], ps[q + 2]);
-      cfma(s3, Gm[(q + 3) * LDP + pl], ps[q + 3]);
+      cfms(v, Mrow[q], prev[q]);
+      cfms(s1, Mrow[q + 1], prev[q + 1]);
+      cfms(s2, Mrow[q + 2], prev[q + 2]);
+      cfms(s3, Mrow[q + 3], prev[q + 3]);
     }
-    if (k < nsep - 1) {
+    return cadd(cadd(v, s1), cadd(s2, s3));
+  };
+  auto wait_use = [&](int u) {
+    if (ok) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&fl[u % S2], (u / S2) & 1, a.spin));
+    return ok;
+  };
+  auto release = [&](int u) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&em[u % S2]);
+  };
+  // ---- forward half chains
+  if (half == 0) {
+    for (int k = 0; k < m; ++k, ++t) {
+      if (!wait_use(t)) break;
+      if (k > 0) {
+        const C psi = row_apply(myrz[k * W + pl], stage(0, t) + W * LDP + pl * LDP, myrz + (k - 1) * W);
+        __syncwarp();
+        if (lane < W) myrz[k * W + lane] = psi;
+      }
+      release(t);
+    }
+  } else {
+    for (int u = 0; u < nb; ++u, ++t) {
+      const int k = K - 1 - u;
+      if (!wait_use(t)) break;
+      if (k < K - 1) {
+        const C psi = row_apply(myrz[k * W + pl], stage(1, t) + W * LDP + pl * LDP, myrz + (k + 1) * W);
+        __syncwarp();
+        if (lane < W) myrz[k * W + lane] = psi;
+      }
+      release(t);
+    }
+  }
+  ok = pair_barrier_and(1 + rhs, ok);
+  // ---- twist (top warp)
+  C fcol[W];
+  if (half == 0 && ok) {
+    if (wait_use(t)) {
+      const C* Gm = stage(0, t);
+      C v = myrz[m * W + pl];
+      if (m >= 1) v = row_apply(v, Gm + W * LDP + pl * LDP, myrz + (m - 1) * W);
+      if (m < K - 1) v = row_apply(v, Gm + 2 * W * LDP + pl * LDP, myrz + (m + 1) * W);
+      __syncwarp();
+      if (lane < W) xch[lane] = v;
+      __syncwarp();
+      C s0{0, 0}, s1{0, 0};
 #pragma unroll
-      for (int q = 0; q < W; q += 4) {   // x_{k+1} from the exchange slot
+      for (int q = 0; q < W; q += 2) {     // Gamma_m is symmetric: lane p reads column p
+        cfma(s0, Gm[q * LDP + pl], xch[q]);
+        cfma(s1, Gm[(q + 1) * LDP + pl], xch[q + 1]);
+      }
+      const C x = cadd(s0, s1);
+#pragma unroll
+      for (int q = 0; q < W; ++q) fcol[q] = Gm[W * LDP + q * LDP + pl];   // F_m column p
+      __syncwarp();
+      if (lane < W) { xm[lane] = x; xch[lane] = x; }
+      if (valid && lane < W) xsb[((fb + m) * a.R + r) * W + lane] = x;
+      release(t);
+      ++t;
+    }
+  }
+  ok = pair_barrier_and(1 + rhs, ok);
+  // ---- backward half chains
+  if (half == 0 && ok) {
+    for (int k = m - 1; k >= 0; --k, ++t) {
+      if (!wait_use(t)) break;
+      const C* Gm = stage(0, t);
+      const C* ps = myrz + k * W;
+      C s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
+#pragma unroll
+      for (int q = 0; q < W; q += 4) {
+        cfma(s0, Gm[q * LDP + pl], ps[q]);
+        cfma(s1, Gm[(q + 1) * LDP + pl], ps[q + 1]);
+        cfma(s2, Gm[(q + 2) * LDP + pl], ps[q + 2]);
+        cfma(s3, Gm[(q + 3) * LDP + pl], ps[q + 3]);
+      }
+#pragma unroll
+      for (int q = 0; q < W; q += 4) {   // - F_{k+1}^t x_{k+1}
         cfms(s0, fcol[q], xch[q]);
         cfms(s1, fcol[q + 1], xch[q + 1]);
         cfms(s2, fcol[q + 2], xch[q + 2]);
         cfms(s3, fcol[q + 3], xch[q + 3]);
       }
-    }
-    const C x = cadd(cadd(s0, s1), cadd(s2, s3));
+      const C x = cadd(cadd(s0, s1), cadd(s2, s3));
 #pragma unroll
-    for (int q = 0; q < W; ++q) fcol[q] = F[q * LDP + pl];
-    __syncwarp();
-    if (lane < W) xch[lane] = x;
-    if (valid && lane < W) xsb[((fb + k) * a.R + r) * W + lane] = x;
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[t % S2]);
+      for (int q = 0; q < W; ++q) fcol[q] = Gm[W * LDP + q * LDP + pl];
+      __syncwarp();
+      if (lane < W) xch[lane] = x;
+      if (valid && lane < W) xsb[((fb + k) * a.R + r) * W + lane] = x;
+      release(t);
+    }
+  } else if (half == 1 && ok && nb > 0) {
+    // F'_m column from the twist slot, then k = m+1 .. K-1
+    if (wait_use(t)) {
+      const C* Gm = stage(1, t);
+#pragma unroll
+      for (int q = 0; q < W; ++q) fcol[q] = Gm[2 * W * LDP + q * LDP + pl];
+      __syncwarp();
+      if (lane < W) xch[lane] = xm[lane];
+      release(t);
+      ++t;
+      for (int k = m + 1; k < K; ++k, ++t) {
+        if (!wait_use(t)) break;
+        const C* Gk = stage(1, t);
+        const C* ps = myrz + k * W;
+        C s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
+#pragma unroll
+        for (int q = 0; q < W; q += 4) {
+          cfma(s0, Gk[q * LDP + pl], ps[q]);
+          cfma(s1, Gk[(q + 1) * LDP + pl], ps[q + 1]);
+          cfma(s2, Gk[(q + 2) * LDP + pl], ps[q + 2]);
+          cfma(s3, Gk[(q + 3) * LDP + pl], ps[q + 3]);
+        }
+#pragma unroll
+        for (int q = 0; q < W; q += 4) {   // - F'_{k-1}^t x_{k-1}
+          cfms(s0, fcol[q], xch[q]);
+          cfms(s1, fcol[q + 1], xch[q + 1]);
+          cfms(s2, fcol[q + 2], xch[q + 2]);
+          cfms(s3, fcol[q + 3], xch[q + 3]);
+        }
+        const C x = cadd(cadd(s0, s1), cadd(s2, s3));
+#pragma unroll
+        for (int q = 0; q < W; ++q) fcol[q] = Gk[W * LDP + q * LDP + pl];
+        __syncwarp();
+        if (lane < W) xch[lane] = x;
+        if (valid && lane < W) xsb[((fb + k) * a.R + r) * W + lane] = x;
+        release(t);
+      }
+    }
   }
   if (!ok && lane == 0) set_status(a.status, HS_ETIMEOUT, front, -2);
 }
@@ -807,7 +923,7 @@ int run_stage_w(const Plan& p, SweepArgs a, cudaStream_t s) {
   if (a.P > 1) {
     dim3 g2(1, (a.R + WPC - 1) / WPC, a.nfront);
     note_launch();
-    phase2_kernel<R, W><<<g2, NT + 32, phase2_smem<R, W>(a.P - 1), s>>>(a);
+    phase2_kernel<R, W><<<g2, NC2 * 32 + 64, phase2_smem<R, W>(a.P - 1), s>>>(a);
   }
   note_launch();
   phase3_kernel<R, W><<<g13, TL::NCONS + 32, sm3, s>>>(a);

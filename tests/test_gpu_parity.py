@@ -88,6 +88,9 @@ APPLY_CASES = [
     (45, 5, 5, 2, 2, 1),      # minimum chunk length, one RHS
     (13, 6, 6, 3, 4, 2),      # n = 2 bp + 1: no lower/upper blocks, F, E and the middle only
     (41, 4, 4, 20, 6, 3),     # d larger than a front: one remainder block per front
+    (31, 5, 5, 2, 16, 2),     # two chunks: one separator (twist only)
+    (47, 5, 5, 3, 16, 2),     # three chunks: twist with a top chain and no bottom chain
+    (79, 6, 6, 4, 8, 3),      # ten chunks: both half chains
 ]
 
 
