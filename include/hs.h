@@ -52,7 +52,9 @@ typedef struct {
   double pml_C;          /* C of Eq. sigma (PML strength, same for boundary and moving PMLs).         default 20 */
   int layers_per_step;   /* d of Sec. 2.3 (rows eliminated per sweep step).                           default 12 */
   int factor_prec;       /* HS_C64: complex float factors and sweep; HS_C128: complex double.          default HS_C64 */
-  int chunk;             /* x1 columns per partition chunk (>= 2; raised to ceil(n/65); 0 = 32).     default 0 */
+  int chunk;             /* x1 columns per partition chunk (>= 2).  0: ceil(n / (SMs/2)), one chunk
+                            CTA per SM pair and front (a full wave); any length is raised until the
+                            separator count fits the separator solve's shared memory.        default 0 */
   int max_nrhs;          /* largest nrhs any later call will use (workspace is sized at setup).       default 64 */
   int restart;           /* FGMRES restart length m.                                                  default 20 */
   int reorth;            /* 0: classical Gram-Schmidt; 1: CGS with a second pass when needed (DGKS).  default 0 */
@@ -160,7 +162,7 @@ int hs_apply(hs_plan* plan, const void* r, void* z, int nrhs, int dtype, void* s
  * problem does not fit: n*n*nrhs + 2*n*nrhs*Wmax + 8*P*nrhs*Wmax elements of
  * the factor precision (Wmax <= 32 the padded window height, P the number of
  * x1 chunks), each rounded up to 256 bytes, must not exceed 32 MiB (for
- * example n = 511 with up to 14 right-hand sides in complex64).
+ * example n = 511 with up to 13 right-hand sides in complex64).
  * Arguments as hs_apply.
  */
 int hs_apply_noalloc(hs_plan* plan, const void* r, void* z, int nrhs, int dtype, void* stream);

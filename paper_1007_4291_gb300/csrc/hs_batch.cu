@@ -151,10 +151,20 @@ extern "C" int hs_autotune(const double* c, double omega, int n, int dim, int pm
   opt.max_nrhs = nrhs;
   opt.tune_cache = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
-  const int lmin = std::max(2, (n + 64) / 65);
+  const int lmin = 2;
   std::vector<int> cand;
+  int dev = 0, sms = 2;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // lengths that give one chunk CTA per pair of SMs (one full wave), per SM,
+  // and a set of fixed lengths (setup raises a length that needs too many
+  // separators)
+  for (int per_front : {std::max(1, sms / 2), std::max(1, sms), std::max(1, sms / 4)}) {
+    const int L = std::max(lmin, (n + per_front - 1) / per_front);
+    if (L <= n && std::find(cand.begin(), cand.end(), L) == cand.end()) cand.push_back(L);
+  }
   for (int L : {8, 12, 16, 24, 32, 48, 64, 96, 128})
-    if (L >= lmin && L <= n) cand.push_back(L);
+    if (L >= lmin && L <= n && std::find(cand.begin(), cand.end(), L) == cand.end()) cand.push_back(L);
   if (cand.empty()) cand.push_back(std::min(n, std::max(lmin, 2)));
   const size_t bytes = (size_t)n * n * nrhs * (opt.factor_prec == HS_C64 ? 8 : 16);
   void* buf = nullptr;

@@ -163,6 +163,9 @@ void release_sweep_graphs(Plan& p);
 int tuned_chunk(const char* path, int n, int bp, int b, int dL, int prec, int nrhs);
 // drop cached multi-plan graphs that contain plan `uid` (hs_batch.cu)
 void forget_batch_graphs(long long uid);
+// largest separator count per x1 partition the separator solve supports for
+// window height W (shared-memory bound)
+int max_separators(int W, int prec);
 // set the shared-memory attributes of every sweep kernel (before a capture)
 void sweep_prepare_attributes(int prec);
 int layout_to_internal(const void* src, int dtype, void* dst, int prec, int n2, int R, cudaStream_t s);

@@ -275,15 +275,24 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
     if (d.W < 0) { delete p; return HS_EUNSUPPORTED; }
     Wmax = std::max(Wmax, d.W);
   }
-  // x1 chunking of the subproblem solves (>= 2 columns per chunk).
-  // (at most 64 separators: the separator solve keeps their right-hand
-  // sides in shared memory)
+  // x1 chunking of the subproblem solves (>= 2 columns per chunk).  Default:
+  // one chunk CTA of each front per pair of SMs, so that a sweep stage's
+  // 2 P chunk CTAs fill the GPU in one wave.  The separator solve keeps the
+  // right-hand sides of all separators of a chain in shared memory, which
+  // bounds the separator count.
   int chunk = opt.chunk;
   if (chunk == 0) chunk = tuned_chunk(opt.tune_cache, n, pml_width, moving_pml_width, opt.layers_per_step,
                                       opt.factor_prec, opt.max_nrhs);
   p->opt.tune_cache = nullptr;  // the string belongs to the caller
-  p->L = chunk ? chunk : 32;
-  p->L = std::max(p->L, (n + 64) / 65);
+  if (!chunk) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 2) sms = 2;
+    const int per_front = sms / 2;
+    chunk = (n + per_front - 1) / per_front;
+  }
+  p->L = chunk;
+  p->L = std::max(p->L, (n + max_separators(Wmax, opt.factor_prec)) / (max_separators(Wmax, opt.factor_prec) + 1));
   if (p->L > n) p->L = n;
   if (p->L < 2) p->L = 2;
   p->P = (n + p->L - 1) / p->L;

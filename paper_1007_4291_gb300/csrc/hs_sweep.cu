@@ -1022,6 +1022,29 @@ int relayout(const void* src, void* dst, long long npts, int R, cudaStream_t s) 
 
 }  // namespace
 
+namespace {
+template <typename R, int W>
+int max_sep_w() {
+  int k = 1;
+  while (k < 4096 && phase2_smem<R, W>(k + 1) <= 220 * 1024) ++k;
+  return k;
+}
+template <typename R>
+int max_sep_r(int W) {
+  switch (W) {
+    case 8: return max_sep_w<R, 8>();
+    case 12: return max_sep_w<R, 12>();
+    case 16: return max_sep_w<R, 16>();
+    case 24: return max_sep_w<R, 24>();
+    default: return max_sep_w<R, 32>();
+  }
+}
+}  // namespace
+
+int max_separators(int W, int prec) {
+  return prec == HS_C64 ? max_sep_r<float>(W) : max_sep_r<double>(W);
+}
+
 void sweep_prepare_attributes(int prec) {
   if (prec == HS_C64) set_attrs<float>(); else set_attrs<double>();
 }
