@@ -49,7 +49,9 @@ enum { HS_C64 = 64, HS_C128 = 128 };
 /* Tuning and method constants.  hs_default_options() fills the defaults. */
 typedef struct {
   double alpha;          /* alpha of Eq. helmalpha: the subproblems use (omega + i alpha)^2 / c^2.   default 2 */
-  double pml_C;          /* C of Eq. sigma (PML strength, same for boundary and moving PMLs).         default 20 */
+  double pml_C;          /* C of Eq. sigma: strength of the boundary PML (part of the operator A).    default 20 */
+  double moving_pml_C;   /* strength of the moving PMLs of the subproblems (Eq. helma): a parameter
+                            of the preconditioner only.                                          default 40 */
   int layers_per_step;   /* d of Sec. 2.3 (rows eliminated per sweep step).                           default 12 */
   int factor_prec;       /* HS_C64: complex float factors and sweep; HS_C128: complex double.          default HS_C64 */
   int chunk;             /* x1 columns per partition chunk (>= 2).  0: ceil(n / (SMs/2)), one chunk

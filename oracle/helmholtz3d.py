@@ -106,10 +106,10 @@ def helmholtz_matrix(c, omega, bp, C, alpha=0.0):
     return assemble(coefficients(c, omega, bp, C, alpha))
 
 
-def window_x3_stretch(blk, n, bp, b, C, omega, full_window=False):
+def window_x3_stretch(blk, n, bp, b, C, omega, full_window=False, Cm=None):
     """x3 stretch of H_B on the window layers (integer and half points),
     the moving profile of Eq. helma3 (same rules as the 2D x2 stretch)."""
-    return S2.window_x2_stretch(blk, n, bp, b, C, omega, full_window)
+    return S2.window_x2_stretch(blk, n, bp, b, C, omega, full_window, Cm)
 
 
 @dataclass
@@ -132,10 +132,10 @@ class FactoredSlab:
         return x[:, off:off + d].copy()
 
 
-def factor_slab(blk, c, omega, bp, b, C, alpha, full_window=False):
+def factor_slab(blk, c, omega, bp, b, C, alpha, full_window=False, Cm=None):
     """Sparse LU of the slab problem H_B (Eq. helma3 on the window)."""
     n = c.shape[1]
-    s3 = window_x3_stretch(blk, n, bp, b, C, omega, full_window)
+    s3 = window_x3_stretch(blk, n, bp, b, C, omega, full_window, Cm)
     cw = c[blk.wlo - 1:blk.whi]
     Hm = assemble(coefficients(cw, omega, bp, C, alpha, s3=s3)).tocsc()
     return FactoredSlab(blk, spla.splu(Hm), n)
@@ -150,12 +150,12 @@ class Setup:
     Ucoup: np.ndarray     # coupling of layer k to k+1, shape (n, n, n) [k-1, j-1, i-1]
 
 
-def setup(c, omega, bp, b, dL, alpha, C, full_window=False):
+def setup(c, omega, bp, b, dL, alpha, C, full_window=False, Cm=None):
     """Algorithm 5 with two fronts and d layers per step: factor every slab."""
     c = np.asarray(c, dtype=np.float64)
     n = c.shape[0]
     lower, upper, middle = S2.partition(n, bp, b, dL, full_window)
-    f = lambda blk: factor_slab(blk, c, omega, bp, b, C, alpha, full_window)
+    f = lambda blk: factor_slab(blk, c, omega, bp, b, C, alpha, full_window, Cm)
     coef = coefficients(c, omega, bp, C, alpha)
     return Setup(n, [f(B) for B in lower], [f(B) for B in upper], f(middle), coef["U"])
 

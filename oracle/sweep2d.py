@@ -108,13 +108,16 @@ def moving_sigma(t, eta_b, C):
     return out
 
 
-def window_x2_stretch(blk, n, bp, b, C, omega, full_window=False):
+def window_x2_stretch(blk, n, bp, b, C, omega, full_window=False, Cm=None):
     """x2 stretch of H_B on the window rows and at the half points.
 
     Returns (s_int, s_up, s_dn) of length w: s2 at rows wlo..whi, at (j+1/2)
     and at (j-1/2).  F, E and full-window blocks use the original boundary
-    profile; moving blocks use the moving profile of Eq. helma.
+    profile (strength C, part of A); moving blocks use the moving profile of
+    Eq. helma with strength Cm (a parameter of the preconditioner only;
+    None = C).
     """
+    Cm = C if Cm is None else Cm
     h = 1.0 / (n + 1)
     j = np.arange(blk.wlo, blk.whi + 1, dtype=np.float64)
     if blk.kind in ("F", "E") or full_window:
@@ -124,25 +127,25 @@ def window_x2_stretch(blk, n, bp, b, C, omega, full_window=False):
         eta_b = b * h
         if blk.kind == "lower":
             d0 = blk.lo - b
-            sig = lambda x: moving_sigma(x - d0 * h, eta_b, C)
+            sig = lambda x: moving_sigma(x - d0 * h, eta_b, Cm)
         elif blk.kind == "upper":
             d1 = blk.hi + b
-            sig = lambda x: moving_sigma(d1 * h - x, eta_b, C)
+            sig = lambda x: moving_sigma(d1 * h - x, eta_b, Cm)
         else:
             d0, d1 = blk.lo - b, blk.hi + b
-            sig = lambda x: moving_sigma(x - d0 * h, eta_b, C) + moving_sigma(d1 * h - x, eta_b, C)
+            sig = lambda x: moving_sigma(x - d0 * h, eta_b, Cm) + moving_sigma(d1 * h - x, eta_b, Cm)
     s_int = H.stretch(sig(j * h), omega)
     s_up = H.stretch(sig((j + 0.5) * h), omega)
     s_dn = H.stretch(sig((j - 0.5) * h), omega)
     return s_int, s_up, s_dn
 
 
-def window_coefficients(blk, c, omega, bp, b, C, alpha, full_window=False):
+def window_coefficients(blk, c, omega, bp, b, C, alpha, full_window=False, Cm=None):
     """Eq. helmd coefficients of H_B (Eq. helma discretised on the window)."""
     n = c.shape[0]
     h = 1.0 / (n + 1)
     s1 = H.axis_stretch(n, bp, C, omega)
-    s_int, s_up, s_dn = window_x2_stretch(blk, n, bp, b, C, omega, full_window)
+    s_int, s_up, s_dn = window_x2_stretch(blk, n, bp, b, C, omega, full_window, Cm)
     rows = np.arange(blk.wlo, blk.whi + 1)
     return H.row_coefficients(c[rows - 1, :], omega, alpha, h, s1, s_int, s_up, s_dn)
 
@@ -201,9 +204,9 @@ class FactoredBlock:
         return np.transpose(x[:, :, off:off + (blk.hi - blk.lo + 1)], (0, 2, 1)).copy()
 
 
-def factor_block(blk, c, omega, bp, b, C, alpha, full_window=False):
+def factor_block(blk, c, omega, bp, b, C, alpha, full_window=False, Cm=None):
     """One step of Algorithm 3: LU of P_B H_B P_B^t (LAPACK band LU)."""
-    coef = window_coefficients(blk, c, omega, bp, b, C, alpha, full_window)
+    coef = window_coefficients(blk, c, omega, bp, b, C, alpha, full_window, Cm)
     ab, kl, ku = band_matrix_x2_first(coef)
     lu, ipiv, info = lapack.zgbtrf(ab, kl, ku)
     if info != 0:
@@ -220,12 +223,13 @@ class Setup:
     Ncoup: np.ndarray      # N_{i,j} of A: coupling (i,j) -> (i,j+1), shape (n, n) [j-1, i-1]
 
 
-def setup(c, omega, bp, b, dL, alpha, C, full_window=False):
-    """Algorithm 3 (two-front, d layers per step): factor every block."""
+def setup(c, omega, bp, b, dL, alpha, C, full_window=False, Cm=None):
+    """Algorithm 3 (two-front, d layers per step): factor every block.
+    Cm: strength of the moving PMLs (None = C)."""
     c = np.asarray(c, dtype=np.float64)
     n = c.shape[0]
     lower, upper, middle = partition(n, bp, b, dL, full_window)
-    f = lambda blk: factor_block(blk, c, omega, bp, b, C, alpha, full_window)
+    f = lambda blk: factor_block(blk, c, omega, bp, b, C, alpha, full_window, Cm)
     coef = H.stencil_coefficients(c, omega, bp, C, alpha)
     return Setup(n, [f(B) for B in lower], [f(B) for B in upper], f(middle), coef["N"])
 

@@ -721,8 +721,8 @@ int prepare_plan3(Plan& p) {
     auto sig = [&](double x) {
       if (d.kind == BK_F || d.kind == BK_E) return sigma_b(x, eta, C);
       double sg = 0.0;
-      if (d.kind == BK_LOWER || d.kind == BK_MIDDLE) sg += sigma_m(x - (d.lo - p.b) * h, eta_b, C);
-      if (d.kind == BK_UPPER || d.kind == BK_MIDDLE) sg += sigma_m((d.hi + p.b) * h - x, eta_b, C);
+      if (d.kind == BK_LOWER || d.kind == BK_MIDDLE) sg += sigma_m(x - (d.lo - p.b) * h, eta_b, p.Cm);
+      if (d.kind == BK_UPPER || d.kind == BK_MIDDLE) sg += sigma_m((d.hi + p.b) * h - x, eta_b, p.Cm);
       return sg;
     };
     auto inv = [&](double sg) { return zc(1.0, sg / p.omega); };

@@ -72,7 +72,7 @@ struct BlockDesc {
 // ---------------------------------------------------------------- plan
 struct Plan {
   int n = 0, dim = 2, bp = 0, b = 0, dL = 1;
-  double omega = 0, alpha = 0, C = 0, h = 0;
+  double omega = 0, alpha = 0, C = 0, Cm = 0, h = 0;   // C boundary PML, Cm moving PMLs
   int prec = HS_C64;  // factor precision
   int L = 32, P = 1;  // x1 chunk length and chunk count
   int max_nrhs = 64;

@@ -110,6 +110,7 @@ extern "C" int hs_default_options(hs_options* opt) {
   if (!opt) return HS_EINVAL;
   opt->alpha = 2.0;
   opt->pml_C = 20.0;
+  opt->moving_pml_C = 40.0;
   opt->layers_per_step = 12;
   opt->factor_prec = HS_C64;
   opt->chunk = 0;
@@ -196,7 +197,7 @@ static int prepare_plan3d(const double* c, double omega, int n, int pml_width, i
   hs_options opt;
   hs_default_options(&opt);
   if (opt_in) opt = *opt_in;
-  if (!(opt.alpha >= 0.0) || !(opt.pml_C >= 0.0) || opt.layers_per_step < 1 || opt.max_nrhs < 1 ||
+  if (!(opt.alpha >= 0.0) || !(opt.pml_C >= 0.0) || !(opt.moving_pml_C >= 0.0) || opt.layers_per_step < 1 || opt.max_nrhs < 1 ||
       opt.max_nrhs > 4096 || opt.restart < 1)
     return HS_EINVAL;
   if (opt.factor_prec != HS_C64 && opt.factor_prec != HS_C128) return HS_EINVAL;
@@ -206,7 +207,7 @@ static int prepare_plan3d(const double* c, double omega, int n, int pml_width, i
     if (!(c[k] > 0.0) || !std::isfinite(c[k])) return HS_EINVAL;
   Plan* p = new Plan();
   p->n = n; p->dim = 3; p->bp = pml_width; p->b = moving_pml_width; p->dL = opt.layers_per_step;
-  p->omega = omega; p->alpha = opt.alpha; p->C = opt.pml_C; p->h = 1.0 / (n + 1);
+  p->omega = omega; p->alpha = opt.alpha; p->C = opt.pml_C; p->Cm = opt.moving_pml_C; p->h = 1.0 / (n + 1);
   p->prec = opt.factor_prec; p->max_nrhs = opt.max_nrhs; p->opt = opt;
   p->opt.tune_cache = nullptr;
   build_blocks(*p);
@@ -256,7 +257,7 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
   hs_options opt;
   hs_default_options(&opt);
   if (opt_in) opt = *opt_in;
-  if (!(opt.alpha >= 0.0) || !(opt.pml_C >= 0.0) || opt.layers_per_step < 1 || opt.max_nrhs < 1 ||
+  if (!(opt.alpha >= 0.0) || !(opt.pml_C >= 0.0) || !(opt.moving_pml_C >= 0.0) || opt.layers_per_step < 1 || opt.max_nrhs < 1 ||
       opt.max_nrhs > 4096 || opt.restart < 1 || opt.chunk < 0 || opt.chunk == 1 || opt.spin_budget < 1)
     return HS_EINVAL;
   if (opt.factor_prec != HS_C64 && opt.factor_prec != HS_C128) return HS_EINVAL;
@@ -267,7 +268,7 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
 
   Plan* p = new Plan();
   p->n = n; p->dim = dim; p->bp = pml_width; p->b = moving_pml_width; p->dL = opt.layers_per_step;
-  p->omega = omega; p->alpha = opt.alpha; p->C = opt.pml_C; p->h = 1.0 / (n + 1);
+  p->omega = omega; p->alpha = opt.alpha; p->C = opt.pml_C; p->Cm = opt.moving_pml_C; p->h = 1.0 / (n + 1);
   p->prec = opt.factor_prec; p->max_nrhs = opt.max_nrhs; p->opt = opt;
   build_blocks(*p);
   int Wmax = 0;
@@ -299,7 +300,7 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
 
   int st = HS_OK;
   auto fail = [&](int s) { free_plan_memory(p); delete p; return s; };
-  const double h = p->h, eta = p->bp * h, eta_b = p->b * h, C = p->C;
+  const double h = p->h, eta = p->bp * h, eta_b = p->b * h, C = p->C, Cm = p->Cm;
 
   // ---- 1D tables of the x1 and x2 axes (Eq. sigma, both axes two-sided)
   std::vector<c128> inv_s(n + 2), a_half(n + 1);
@@ -379,8 +380,8 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
     auto sig = [&](double x) {
       if (d.kind == BK_F || d.kind == BK_E) return sigma_boundary(x, eta, C);
       double s = 0.0;
-      if (d.kind == BK_LOWER || d.kind == BK_MIDDLE) s += sigma_moving(x - (d.lo - p->b) * h, eta_b, C);
-      if (d.kind == BK_UPPER || d.kind == BK_MIDDLE) s += sigma_moving((d.hi + p->b) * h - x, eta_b, C);
+      if (d.kind == BK_LOWER || d.kind == BK_MIDDLE) s += sigma_moving(x - (d.lo - p->b) * h, eta_b, Cm);
+      if (d.kind == BK_UPPER || d.kind == BK_MIDDLE) s += sigma_moving((d.hi + p->b) * h - x, eta_b, Cm);
       return s;
     };
     for (int q = 0; q < d.w; ++q) s2win.push_back(to_c(inv_stretch(sig((d.wlo + q) * h), omega)));

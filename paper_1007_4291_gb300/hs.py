@@ -27,7 +27,8 @@ HS_CNN_NPARAM = 10434
 
 
 class HsOptions(ctypes.Structure):
-    _fields_ = [("alpha", ctypes.c_double), ("pml_C", ctypes.c_double), ("layers_per_step", ctypes.c_int),
+    _fields_ = [("alpha", ctypes.c_double), ("pml_C", ctypes.c_double), ("moving_pml_C", ctypes.c_double),
+                ("layers_per_step", ctypes.c_int),
                 ("factor_prec", ctypes.c_int), ("chunk", ctypes.c_int), ("max_nrhs", ctypes.c_int),
                 ("restart", ctypes.c_int), ("reorth", ctypes.c_int), ("spin_budget", ctypes.c_longlong),
                 ("graphs", ctypes.c_int), ("krylov_basis", ctypes.c_int), ("inner_tol", ctypes.c_double),

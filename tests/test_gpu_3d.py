@@ -18,6 +18,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 C_PML = 20.0
+C_MOVING = 40.0      # library default strength of the moving PMLs
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -92,7 +93,7 @@ def test_apply3_matches_oracle(case, mode):
         torch.cuda.synchronize()
         assert hs.hs_last_device_status(p) == hs.HS_OK
         z = zg.cpu().numpy().astype(np.complex128)
-        st = H3.setup(c, omega, bp, b, dL, alpha, C_PML)
+        st = H3.setup(c, omega, bp, b, dL, alpha, C_PML, Cm=C_MOVING)
         ref = H3.apply(st, rg.cpu().numpy().astype(np.complex128))
         err = max(relerr(z[k], ref[k]) for k in range(R))
         print("3D apply n=%d prec=%d frontal=%d: max relative error %.3e" % (n, prec, frontal, err))

@@ -20,6 +20,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 C_PML = 20.0
+C_MOVING = 40.0      # library default strength of the moving PMLs
 BP = 6
 
 
@@ -67,7 +68,7 @@ def test_batched_setup_matches_single_setup_and_oracle():
             zb = apply_direct(plans[k], rg, 2).cpu().numpy()
             zs = apply_direct(singles[k], rg, 2).cpu().numpy()
             assert np.array_equal(zb, zs), n          # same per-item arithmetic
-            st = S.setup(cs[k], omega_of(n), BP, BP, 3, 2.0, C_PML)
+            st = S.setup(cs[k], omega_of(n), BP, BP, 3, 2.0, C_PML, Cm=C_MOVING)
             ref = S.apply(st, r.astype(np.complex64).astype(np.complex128))
             assert relerr(zb.astype(np.complex128), ref) <= 1e-4, n
     finally:
@@ -164,7 +165,8 @@ def test_expired_device_wait_is_reported_and_context_stays_usable():
     try:
         r = I.random_rhs(n, 2, 1)
         z = apply_direct(good, torch.from_numpy(r).to("cuda").to(torch.complex64), 2).cpu().numpy()
-        ref = S.apply(S.setup(c, omega_of(n), BP, BP, 3, 2.0, C_PML), r.astype(np.complex64).astype(np.complex128))
+        ref = S.apply(S.setup(c, omega_of(n), BP, BP, 3, 2.0, C_PML, Cm=C_MOVING),
+                      r.astype(np.complex64).astype(np.complex128))
         assert relerr(z.astype(np.complex128), ref) <= 1e-4
     finally:
         hs.hs_destroy(good)

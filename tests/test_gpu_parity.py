@@ -19,6 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 C_PML = 20.0
+C_MOVING = 40.0      # library default strength of the moving PMLs
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -103,7 +104,7 @@ def test_apply_matches_oracle(case, prec):
     plan = make_plan(c, omega, bp, b, dL, prec=prec, chunk=chunk, alpha=alpha)
     try:
         r = I.random_rhs(n, R, 5)
-        st = S.setup(c, omega, bp, b, dL, alpha, C_PML)
+        st = S.setup(c, omega, bp, b, dL, alpha, C_PML, Cm=C_MOVING)
         ref = S.apply(st, r)
         io = hs.HS_C64 if prec == hs.HS_C64 else hs.HS_C128
         rin = r.astype(np.complex64).astype(np.complex128) if io == hs.HS_C64 else r
@@ -124,7 +125,7 @@ def test_apply_c128_io_with_c64_factors_and_alias():
     plan = make_plan(c, omega, bp, bp, 2, chunk=6)
     try:
         r = I.random_rhs(n, 2, 1)
-        ref = S.apply(S.setup(c, omega, bp, bp, 2, 2.0, C_PML), r)
+        ref = S.apply(S.setup(c, omega, bp, bp, 2, 2.0, C_PML, Cm=C_MOVING), r)
         rg = gpu(r)
         hs.hs_apply(plan, rg, rg, 2, hs.HS_C128)
         assert relerr(rg.cpu().numpy(), ref) <= 1e-4
@@ -187,7 +188,7 @@ def test_solve_iteration_count_matches_oracle():
         code, info = hs.hs_solve(plan, fg, ug, 1, 1e-8, 100)
         assert code == hs.HS_OK
         A0 = H.helmholtz_matrix(c, omega, bp, C_PML, 0.0)
-        st = S.setup(c, omega, bp, bp, 2, 2.0, C_PML)
+        st = S.setup(c, omega, bp, bp, 2, 2.0, C_PML, Cm=C_MOVING)
         _, it, _ = K.fgmres(lambda v: A0 @ v, lambda v: S.apply(st, v.reshape(n, n)).ravel(), f[0].ravel(),
                             tol=1e-8, restart=30)
         assert abs(info["iterations"] - it) <= 1

@@ -273,3 +273,28 @@ def test_behaviour_planted_missing_moving_pml(monkeypatch):
     block) the same solve needs far more iterations than the paper's band."""
     monkeypatch.setattr(S, "moving_sigma", lambda t, e, C: np.zeros_like(np.asarray(t, dtype=float)))
     assert _paper_setting_iterations() > 26
+
+
+def test_moving_pml_strength_is_a_preconditioner_parameter():
+    """Cm changes only the moving profiles of the subproblems: F, E keep the
+    boundary profile (their T~ are exact Schur inverses of A's blocks), and
+    Cm = C reproduces the single-constant setup."""
+    from paper_1007_4291_gb300 import inputs as I
+    n, bp, b, dL = 23, 4, 4, 3
+    c = I.random_velocity(n, 3)
+    omega = 2 * np.pi * 2.0
+    r = I.random_rhs(n, 1, 4)[0]
+    base = S.apply(S.setup(c, omega, bp, b, dL, 2.0, 20.0), r)
+    same = S.apply(S.setup(c, omega, bp, b, dL, 2.0, 20.0, Cm=20.0), r)
+    other = S.apply(S.setup(c, omega, bp, b, dL, 2.0, 20.0, Cm=40.0), r)
+    assert np.array_equal(base, same)
+    assert not np.allclose(base, other)
+    lower, upper, _ = S.partition(n, bp, b, dL)
+    for blk in (lower[0], upper[0]):          # F and E
+        s1 = S.window_x2_stretch(blk, n, bp, b, 20.0, omega, Cm=40.0)
+        s0 = S.window_x2_stretch(blk, n, bp, b, 20.0, omega)
+        assert all(np.array_equal(x, y) for x, y in zip(s0, s1))
+    moving = lower[1]
+    s1 = S.window_x2_stretch(moving, n, bp, b, 20.0, omega, Cm=40.0)[0]
+    s0 = S.window_x2_stretch(moving, n, bp, b, 20.0, omega)[0]
+    assert not np.allclose(s0, s1) and np.allclose(s0[-dL:], 1.0) and np.allclose(s1[-dL:], 1.0)
