@@ -173,5 +173,7 @@ int layout_from_internal(const void* src, int prec, void* dst, int dtype, int n2
 int matvec_abi(Plan& p, const void* x, void* y, int nrhs, int dtype, cudaStream_t s);
 // internal-layout FP64 products: y = A x (x c64 or c128), or y = f - A x
 int matvec_internal_f64(Plan& p, const void* x, bool x_is_c64, c128* y, const c128* f, int R, cudaStream_t s);
+// y = A x in FP32 on solver-layout complex64 vectors (2D plans)
+int matvec_internal_f32(Plan& p, const c64* x, c64* y, int R, cudaStream_t s);
 
 }  // namespace hs

@@ -218,23 +218,35 @@ __global__ void scale_df_kernel(const cdf* __restrict__ w, const df* __restrict_
        e += (long long)gridDim.x * blockDim.x)
     v[e] = cdf_scale(w[e], s[e % R]);
 }
+// The RHS index of a grid-stride element loop, advanced by the stride's
+// residue instead of a 64-bit remainder per element.
+struct RhsCursor {
+  int r, step, R;
+  __device__ RhsCursor(long long e0, long long stride, int R_) : r((int)(e0 % R_)), step((int)(stride % R_)), R(R_) {}
+  __device__ void advance() {
+    r += step;
+    if (r >= R) r -= R;
+  }
+};
 __global__ void scale_f32_kernel(const c64* __restrict__ w, const float* __restrict__ s, c64* __restrict__ v,
                                  long long total, int R) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const float f = s[e % R];
+  const long long e0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  RhsCursor rc(e0, stride, R);
+  for (long long e = e0; e < total; e += stride, rc.advance()) {
+    const float f = s[rc.r];
     v[e] = c64{w[e].re * f, w[e].im * f};
   }
 }
 // v = complex64 (r * s[r]) from a double-float vector (the scaled residual
-// that starts a refinement cycle)
-__global__ void df_to_c64_scaled_kernel(const cdf* __restrict__ r, const double* __restrict__ s, c64* __restrict__ v,
+// that starts a refinement cycle; FP32 rounding is all the cycle keeps)
+__global__ void df_to_c64_scaled_kernel(const cdf* __restrict__ r, const float* __restrict__ s, c64* __restrict__ v,
                                         long long total, int R) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const double f = s[e % R];
+  const long long e0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  RhsCursor rc(e0, stride, R);
+  for (long long e = e0; e < total; e += stride, rc.advance()) {
+    const float f = s[rc.r];
     const cdf a = r[e];
-    v[e] = c64{(float)(((double)a.re.h + (double)a.re.l) * f), (float)(((double)a.im.h + (double)a.im.l) * f)};
+    v[e] = c64{(a.re.h + a.re.l) * f, (a.im.h + a.im.l) * f};
   }
 }
 template <typename AR>
@@ -261,6 +273,35 @@ __global__ void __launch_bounds__(KT) xupdate_kernel(const cplx<ZT>* __restrict_
 #pragma unroll
     for (int i = 0; i < MAXJ; ++i)
       if (i < k) AR::add_prod_z(xv, yc[i], Z[i * zstride + e]);
+    x[e] = xv;
+  }
+}
+
+// Refinement update x += d with the cycle's correction d = sum_i y_i Z_i
+// formed in FP32 (it only has to be as accurate as the cycle that made it)
+// and added to the double-float iterate exactly.
+template <int MAXJ>
+__global__ void __launch_bounds__(KT) xcorrect_kernel(const c64* __restrict__ Z, long long zstride, int k,
+                                                      const c128* __restrict__ y, cdf* __restrict__ x,
+                                                      long long npts, int R) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.y * 32 + lane;
+  if (r >= R) return;
+  c64 yc[MAXJ];
+#pragma unroll
+  for (int i = 0; i < MAXJ; ++i) {
+    const c128 v = (i < k) ? y[i * R + r] : c128{0, 0};
+    yc[i] = c64{(float)v.re, (float)v.im};
+  }
+  for (long long pt = (long long)blockIdx.x * 8 + warp; pt < npts; pt += (long long)gridDim.x * 8) {
+    const long long e = pt * R + r;
+    c64 d{0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < MAXJ; ++i)
+      if (i < k) cfma(d, yc[i], Z[i * zstride + e]);
+    cdf xv = x[e];
+    xv.re = df_add(xv.re, df{d.re, 0.f});
+    xv.im = df_add(xv.im, df{d.im, 0.f});
     x[e] = xv;
   }
 }
@@ -862,6 +903,7 @@ int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxi
   for (int r = 0; r < R; ++r) fn[r] = std::sqrt(hbuf[r].re);
   std::vector<zc> H((size_t)R * (m + 1) * m), g((size_t)R * (m + 1)), sn((size_t)R * m);
   std::vector<double> cs((size_t)R * m), relres(R, 1.0), scl(R);
+  std::vector<float> sclf(R);
   std::vector<char> active(R);
   int it = 0, cycles = 0, applies = 0, st = HS_OK;
   void* const u_saved = p.d_u;
@@ -882,9 +924,10 @@ int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxi
     }
     if (all || it >= maxit) break;
     ++cycles;
-    cudaMemcpyAsync(w.s, scl.data(), R * sizeof(double), cudaMemcpyHostToDevice, s);
+    for (int r = 0; r < R; ++r) sclf[r] = (float)scl[r];
+    cudaMemcpyAsync(w.s, sclf.data(), R * sizeof(float), cudaMemcpyHostToDevice, s);
     note_launch();
-    df_to_c64_scaled_kernel<<<sm_count() * 8, 256, 0, s>>>(rb, (const double*)w.s, Vb, vs, R);
+    df_to_c64_scaled_kernel<<<sm_count() * 8, 256, 0, s>>>(rb, (const float*)w.s, Vb, vs, R);
     int k = 0;
     for (int j = 0; j < m; ++j) {
       c64* Vj = Vb + (long long)j * vs;
@@ -898,8 +941,8 @@ int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxi
       if (st != HS_OK) break;
       ++applies;
       cudaEventRecord(ev[1], s);
-      K.matvec(Zj, false, rb, nullptr);        // A z_j in double-float
-      K.to_c64(rb, W1);
+      st = matvec_internal_f32(p, Zj, W1, R, s);   // A z_j in FP32 (the cycle's precision)
+      if (st != HS_OK) break;
       cudaEventRecord(ev[2], s);
       B.dots(Vb, j + 1, W1);                   // FP32 classical Gram-Schmidt
       B.update(Vb, j + 1, W1, 32);
@@ -954,7 +997,13 @@ int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxi
       for (int i = 0; i < k; ++i) y[(size_t)i * R + r] = c128{yr[i].real(), yr[i].imag()};
     }
     cudaMemcpyAsync(w.h, y.data(), y.size() * sizeof(c128), cudaMemcpyHostToDevice, s);
-    K.xupdate(Z, k, x);
+    {
+      const dim3 g = K.grid();
+      note_launch();
+      if (k <= 8) xcorrect_kernel<8><<<g, KT, 0, s>>>(Z, (long long)vs, k, w.h, x, (long long)npts, R);
+      else if (k <= 16) xcorrect_kernel<16><<<g, KT, 0, s>>>(Z, (long long)vs, k, w.h, x, (long long)npts, R);
+      else xcorrect_kernel<32><<<g, KT, 0, s>>>(Z, (long long)vs, k, w.h, x, (long long)npts, R);
+    }
     cudaStreamSynchronize(s);
   }
   p.d_u = u_saved;

@@ -7,6 +7,7 @@
 //
 // One thread per (point, RHS) element; both vector layouts are supported:
 // RHS-outer (the ABI layout, x1 fastest) and RHS-inner (the solver's layout).
+#include <algorithm>
 #include "hs_internal.cuh"
 #include "hs3d.cuh"
 
@@ -65,6 +66,47 @@ __global__ void __launch_bounds__(256) matvec_kernel(const cplx<Tx>* __restrict_
   }
 }
 
+// Solver layout, same arithmetic: one warp per grid point and 32 consecutive
+// RHS, so the point's coordinates and coefficients are warp-uniform and
+// every neighbour load is a contiguous 32-element row segment.
+template <typename Rc>
+__global__ void __launch_bounds__(256) matvec_inner_kernel(const cplx<Rc>* __restrict__ x, cplx<Rc>* __restrict__ y,
+                                                           Tabs<Rc> t, int n, int R) {
+  using C = cplx<Rc>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.y * 32 + lane;
+  if (r >= R) return;
+  const int n2 = n * n;
+  const long long sx = R, sy = (long long)n * R;
+  for (int pt = blockIdx.x * 8 + warp; pt < n2; pt += gridDim.x * 8) {
+    const int j = pt / n, i = pt - j * n;
+    const long long e = (long long)pt * R + r;
+    const C xc = x[e];
+    const C xe = (i + 1 < n) ? x[e + sx] : C{0, 0};
+    const C xw = (i > 0) ? x[e - sx] : C{0, 0};
+    const C xn = (j + 1 < n) ? x[e + sy] : C{0, 0};
+    const C xs = (j > 0) ? x[e - sy] : C{0, 0};
+    const Rc m0 = t.m0[pt];
+    C acc;
+    if (!t.pml1[i + 1] && !t.pml2[j + 1]) {
+      const C sum = cadd(cadd(xe, xw), cadd(xn, xs));
+      const Rc dg = m0 - Rc(4) * t.ih2;
+      acc = C{fma(t.ih2, sum.re, dg * xc.re), fma(t.ih2, sum.im, dg * xc.im)};
+    } else {
+      const C is1 = t.inv_s1[i + 1], is2 = t.inv_s2[j + 1];
+      const C E = cmul(t.a1[i + 1], is2), Wc = cmul(t.a1[i], is2);
+      const C N = cmul(t.a2[j + 1], is1), S = cmul(t.a2[j], is1);
+      const C D = csub(cscale(cmul(is1, is2), m0), cadd(cadd(E, Wc), cadd(N, S)));
+      acc = cmul(D, xc);
+      cfma(acc, E, xe);
+      cfma(acc, Wc, xw);
+      cfma(acc, N, xn);
+      cfma(acc, S, xs);
+    }
+    y[e] = acc;
+  }
+}
+
 template <typename Rc> Tabs<Rc> tabs(const Plan& p);
 template <> Tabs<double> tabs<double>(const Plan& p) {
   return Tabs<double>{p.d_inv_s1, p.d_a1, p.d_inv_s2, p.d_a2, p.d_m0, p.d_pml1, p.d_pml2,
@@ -100,6 +142,23 @@ int matvec_abi(Plan& p, const void* x, void* y, int nrhs, int dtype, cudaStream_
     matvec_kernel<float, float, float, false, false><<<grid_for(total), 256, 0, s>>>(
         (const c64*)x, (c64*)y, nullptr, tabs<float>(p), p.n, nrhs);
   }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HS_OK : cuda_status(e);
+}
+
+int matvec_internal_f32(Plan& p, const c64* x, c64* y, int R, cudaStream_t s) {
+  if (p.dim != 2) return HS_EUNSUPPORTED;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int gy = (R + 31) / 32;
+  const long long want = ((long long)p.n * p.n + 7) / 8;
+  const long long cap = std::max(1LL, (long long)sms * 8 / gy);   // 8 CTAs of 256 per SM
+  note_launch();
+  matvec_inner_kernel<float><<<dim3((unsigned)std::min(want, cap), gy), 256, 0, s>>>(x, y, tabs<float>(p), p.n, R);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HS_OK : cuda_status(e);
 }
