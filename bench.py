@@ -269,34 +269,36 @@ def comparator_fp64(args, wl, stream):
     return out
 
 
-def batched_uneven(stream, nprob=32, nrhs=8):
+def batched_uneven(stream, nprob=32, nrhs=8, big_n=2047, big_nrhs=256):
     """32 problems with n drawn (seed 2) from {255, 383, 511, 767, 1023},
     omega/2pi = (n+1)/16, smooth random velocities (seeds 100+k), 8 point
-    sources each: one batched setup launch and one CUDA-graph application of
-    all 32 sweeps, against one-at-a-time setups and applies."""
+    sources each, plus one n = 2047 problem (omega/2pi = 128, velocity seed 0)
+    with 256 point sources: one batched setup launch (options per problem, so
+    each reserves its own RHS capacity) and one CUDA-graph application of all
+    33 sweeps, against one-at-a-time setups and applies."""
     import torch
     from paper_1007_4291_gb300 import hs
     from paper_1007_4291_gb300 import inputs as I
     rng = np.random.default_rng(2)
-    ns = [int(x) for x in rng.choice([255, 383, 511, 767, 1023], size=nprob)]
-    cs = [I.random_velocity(n, 100 + k).ravel() for k, n in enumerate(ns)]
+    ns = [int(x) for x in rng.choice([255, 383, 511, 767, 1023], size=nprob)] + [big_n]
+    cs = [I.random_velocity(n, 100 + k).ravel() for k, n in enumerate(ns[:-1])] + [I.random_velocity(big_n, 0).ravel()]
     om = [2 * np.pi * (n + 1) / 16.0 for n in ns]
-    opt = hs.hs_default_options(alpha=2.0, pml_C=20.0, layers_per_step=12, max_nrhs=nrhs)
-    rs = [torch.from_numpy(I.point_sources(n, nrhs, 200 + k, 12)).to("cuda").to(torch.complex64)
-          for k, n in enumerate(ns)]
+    nr = [nrhs] * nprob + [big_nrhs]
+    opts = [hs.hs_default_options(alpha=2.0, pml_C=20.0, layers_per_step=12, max_nrhs=q) for q in nr]
+    rs = [torch.from_numpy(I.point_sources(n, q, 200 + k, 12)).to("cuda").to(torch.complex64)
+          for k, (n, q) in enumerate(zip(ns, nr))]
     zs = [torch.empty_like(r) for r in rs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plans = hs.hs_setup_batched(cs, om, ns, 2, 12, 12, opt, stream)
+    plans = hs.hs_setup_batched(cs, om, ns, 2, 12, 12, opts, stream)
     torch.cuda.synchronize()
     t_setup_b = time.perf_counter() - t0
     t0 = time.perf_counter()
-    singles = [hs.hs_setup(c, w, n, 2, 12, 12, opt, stream) for c, w, n in zip(cs, om, ns)]
+    singles = [hs.hs_setup(c, w, n, 2, 12, 12, o, stream) for c, w, n, o in zip(cs, om, ns, opts)]
     torch.cuda.synchronize()
     t_setup_s = time.perf_counter() - t0
     for q in singles:
         hs.hs_destroy(q)
-    nr = [nrhs] * nprob
     hs.hs_apply_batched(plans, rs, zs, nr, hs.HS_C64, stream)      # capture
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 5
@@ -308,18 +310,18 @@ def batched_uneven(stream, nprob=32, nrhs=8):
     t_batched = e0.elapsed_time(e1) / reps
     e0.record(stream)
     for _ in range(reps):
-        for p, r, z in zip(plans, rs, zs):
-            hs.hs_apply(p, r, z, nrhs, hs.HS_C64, stream)
+        for p, r, z, q in zip(plans, rs, zs, nr):
+            hs.hs_apply(p, r, z, q, hs.HS_C64, stream)
     e1.record(stream)
     torch.cuda.synchronize()
     t_seq = e0.elapsed_time(e1) / reps
     st = max(hs.hs_last_device_status(p) for p in plans)
     for p in plans:
         hs.hs_destroy(p)
-    return {"problems": nprob, "nrhs_each": nrhs, "n": ns, "status": st,
+    return {"problems": len(ns), "nrhs": nr, "n": ns, "status": st,
             "setup_batched_ms": t_setup_b * 1e3, "setup_one_at_a_time_ms": t_setup_s * 1e3,
             "apply_graph_ms": t_batched, "apply_one_at_a_time_ms": t_seq,
-            "rhs_applies_per_s": nprob * nrhs / (t_batched / 1e3)}
+            "rhs_applies_per_s": sum(nr) / (t_batched / 1e3)}
 
 
 def three_d(stream, n=63, nrhs=16):
@@ -353,6 +355,38 @@ def three_d(stream, n=63, nrhs=16):
                     "iterations": info["iterations"], "max_relres": info["max_relres"],
                     "ms_per_apply": info["t_apply_ms"] / max(info["applies"], 1)}
         out[name] = best
+    return out
+
+
+def stencil(stream, wl, opt, f_dev, hbm, reps=10):
+    """The 5-point matvec y = A x through hs_matvec (ABI layout, RHS outermost)
+    on the workload's 64 right-hand sides, complex64 and complex128: device
+    time per call and the algorithmic bytes (x read once, y written once, the
+    per-point omega^2/c^2 table) against the measured HBM copy bandwidth."""
+    import torch
+    from paper_1007_4291_gb300 import hs
+
+    n, R = wl["n"], f_dev.shape[0]
+    plan = hs.hs_setup(np.ascontiguousarray(wl["c"].ravel()), wl["omega"], n, 2, wl["bp"], wl["b"], opt, stream)
+    out = {"what": "hs_matvec, %d RHS, n = %d, inputs larger than L2" % (R, n)}
+    try:
+        for name, dtype, x in (("c64", hs.HS_C64, f_dev.to(torch.complex64)), ("c128", hs.HS_C128, f_dev)):
+            y = torch.empty_like(x)
+            for _ in range(2):
+                hs.hs_matvec(plan, x, y, R, dtype, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                hs.hs_matvec(plan, x, y, R, dtype, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            es = x.element_size()
+            by = 2 * R * n * n * es + n * n * es // 2
+            out[name] = {"ms": ms, "bytes": by, "gbs": by / ms / 1e6, "frac_of_measured_hbm": by / ms / 1e6 / hbm}
+            del x, y
+    finally:
+        hs.hs_destroy(plan)
     return out
 
 
@@ -476,6 +510,15 @@ def run_ours(args):
                 "hbm_frac": by / per_apply / 1e9 / hbm,
                 "algorithmic_flops_per_apply": fl, "algorithmic_bytes_per_apply": by,
                 "ms_per_apply": per_apply * 1e3}
+    # stencil matvecs: the FP32 solver-layout matvec of the Arnoldi cycles
+    # (timed inside hs_solve) and hs_matvec on its own
+    mv_calls = sum(i["applies"] for i in infos)
+    t_mv = sum(i["t_matvec_ms"] for i in infos) / 1e3
+    mv_bytes = 2 * R * n * n * 8 + n * n * 4
+    sten = stencil(stream, wl, opt, f_dev, hbm) if rank == 0 else {}
+    sten["solver_fp32"] = {"calls": mv_calls, "ms": t_mv / max(mv_calls, 1) * 1e3, "bytes": mv_bytes,
+                           "gbs": mv_bytes * mv_calls / t_mv / 1e9 if t_mv > 0 else None,
+                           "frac_of_measured_hbm": mv_bytes * mv_calls / t_mv / 1e9 / hbm if t_mv > 0 else None}
     it = [i["iterations"] for i in infos]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -489,7 +532,7 @@ def run_ours(args):
                   "t_matvec_ms": statistics.mean(i["t_matvec_ms"] for i in infos),
                   "t_orth_ms": statistics.mean(i["t_orth_ms"] for i in infos),
                   "t_solve_ms": statistics.mean(i["t_total_ms"] for i in infos)},
-        "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches),
+        "roofline": roofline, "stencil": sten, "clocks": clocks, "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps, "wall_s_timed": wall,
     }
     if e2e is not None:

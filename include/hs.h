@@ -103,7 +103,7 @@ int hs_default_options(hs_options* opt);
  * c        HOST pointer to n^dim velocities c (double, x1 fastest, then x2, x3), c > 0.
  * omega    angular frequency omega > 0 (Sec. 1).
  * n        grid points per axis; odd, so that the two fronts meet at the middle
- *          layer (n+1)/2 (Sec. 2.3).
+ *          layer (n+1)/2 (Sec. 2.3); n <= 32767 in 2D (HS_EUNSUPPORTED above).
  * dim      2, or 3 for the 7-point operator of Sec. 4 (Eq. helmd3) on n^3 points with
  *          the slab sweep of Algorithms 5 and 6 (two fronts in x3, d layers per step;
  *          each slab solved by a nested-dissection multifrontal factorisation of
@@ -135,6 +135,17 @@ int hs_setup(const double* c, double omega, int n, int dim, int pml_width, int m
 int hs_setup_batched(int nprob, const double* const* c, const double* omega, const int* n, int dim,
                      int pml_width, int moving_pml_width, const hs_options* opt, void* stream,
                      hs_plan** plans);
+
+/*
+ * hs_setup_batched_opts -- hs_setup_batched with options per problem: opts
+ * points to nprob hs_options (problem k uses opts[k]), so that problems of
+ * very different sizes can each reserve their own max_nrhs and chunk length
+ * in the same launch.  All entries must name the same factor_prec
+ * (HS_EINVAL otherwise); everything else is as for hs_setup_batched.
+ */
+int hs_setup_batched_opts(int nprob, const double* const* c, const double* omega, const int* n, int dim,
+                          int pml_width, int moving_pml_width, const hs_options* opts, void* stream,
+                          hs_plan** plans);
 
 /*
  * hs_apply -- z = M_alpha r (Algorithm 4 with two fronts, Sec. 2.3).

@@ -85,6 +85,7 @@ struct Plan {
   c128* d_inv_s2 = nullptr; c128* d_a2 = nullptr;
   c64* f_inv_s1 = nullptr; c64* f_a1 = nullptr; c64* f_inv_s2 = nullptr; c64* f_a2 = nullptr;
   unsigned char* d_pml1 = nullptr; unsigned char* d_pml2 = nullptr;  // 1 = PML affects column i / row j
+  int int_lo = 0, int_hi = 0;   // 0-based index range of points no PML affects (same on both axes; empty if none)
   double* d_m0 = nullptr;   // omega^2 / c^2 per point
   float* f_m0 = nullptr;
   double* d_cinv2 = nullptr; // 1/c^2 per point

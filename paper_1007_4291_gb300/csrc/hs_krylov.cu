@@ -228,25 +228,30 @@ struct RhsCursor {
     if (r >= R) r -= R;
   }
 };
-__global__ void scale_f32_kernel(const c64* __restrict__ w, const float* __restrict__ s, c64* __restrict__ v,
-                                 long long total, int R) {
+// v = w * s[r], also written to v2 when given (the next sweep's input)
+__global__ void scale_f32_kernel(const c64* w, const float* __restrict__ s, c64* v, long long total, int R,
+                                 c64* __restrict__ v2 = nullptr) {
   const long long e0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
   RhsCursor rc(e0, stride, R);
   for (long long e = e0; e < total; e += stride, rc.advance()) {
     const float f = s[rc.r];
-    v[e] = c64{w[e].re * f, w[e].im * f};
+    const c64 a{w[e].re * f, w[e].im * f};
+    v[e] = a;
+    if (v2) v2[e] = a;
   }
 }
 // v = complex64 (r * s[r]) from a double-float vector (the scaled residual
 // that starts a refinement cycle; FP32 rounding is all the cycle keeps)
 __global__ void df_to_c64_scaled_kernel(const cdf* __restrict__ r, const float* __restrict__ s, c64* __restrict__ v,
-                                        long long total, int R) {
+                                        long long total, int R, c64* __restrict__ v2) {
   const long long e0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
   RhsCursor rc(e0, stride, R);
   for (long long e = e0; e < total; e += stride, rc.advance()) {
     const float f = s[rc.r];
     const cdf a = r[e];
-    v[e] = c64{(a.re.h + a.re.l) * f, (a.im.h + a.im.l) * f};
+    const c64 b{(a.re.h + a.re.l) * f, (a.im.h + a.im.l) * f};
+    v[e] = b;
+    v2[e] = b;
   }
 }
 template <typename AR>
@@ -360,17 +365,20 @@ __device__ __forceinline__ cdf ld_x(const void* x, long long k) {
   return cdf{df{v.re, 0.f}, df{v.im, 0.f}};
 }
 
+// One warp per grid point and 32 consecutive RHS (coordinates and
+// coefficients warp-uniform, neighbour rows contiguous).
 template <bool XDF, bool RESID>
 __global__ void __launch_bounds__(256) matvec_df_kernel(const void* __restrict__ x, cdf* __restrict__ y,
                                                         const cdf* __restrict__ f, DfTabs t, int n, int R) {
-  const long long n2 = (long long)n * n;
-  const long long total = n2 * R;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.y * 32 + lane;
+  if (r >= R) return;
+  const int n2 = n * n;
   const cdf zero{df{0.f, 0.f}, df{0.f, 0.f}};
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long pt = e / R;
-    const int j = (int)(pt / n), i = (int)(pt - (long long)j * n);
-    const long long sx = R, sy = (long long)n * R;
+  const long long sx = R, sy = (long long)n * R;
+  for (int pt = blockIdx.x * 8 + warp; pt < n2; pt += gridDim.x * 8) {
+    const int j = pt / n, i = pt - j * n;
+    const long long e = (long long)pt * R + r;
     const cdf xc = ld_x<XDF>(x, e);
     const cdf xe = (i + 1 < n) ? ld_x<XDF>(x, e + sx) : zero;
     const cdf xw = (i > 0) ? ld_x<XDF>(x, e - sx) : zero;
@@ -399,11 +407,6 @@ __global__ void __launch_bounds__(256) matvec_df_kernel(const void* __restrict__
   }
 }
 
-int grid1(long long total) {
-  long long g = (total + 255) / 256;
-  long long cap = (long long)sm_count() * 32;
-  return (int)(g < cap ? g : cap);
-}
 
 // ---------------------------------------------------------------- workspace
 // Process-wide Krylov workspace: one device allocation reused by every
@@ -596,7 +599,8 @@ struct Solver {
     } else {
       DfTabs t{(const cdf*)p.k_inv_s1, (const cdf*)p.k_a1, (const cdf*)p.k_inv_s2, (const cdf*)p.k_a2,
                (const df*)p.k_m0, p.d_pml1, p.d_pml2, (float)((double)(p.n + 1) * (p.n + 1))};
-      const int g = grid1(vs);
+      const int gy = (R + 31) / 32;
+      const dim3 g((unsigned)std::min<long long>(((long long)p.n * p.n + 7) / 8, std::max(1, sm_count() * 8 / gy)), gy);
       note_launch();
       if (solver_vec) {
         if (f) matvec_df_kernel<true, true><<<g, 256, 0, s>>>(x, y, f, t, p.n, R);
@@ -927,15 +931,13 @@ int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxi
     for (int r = 0; r < R; ++r) sclf[r] = (float)scl[r];
     cudaMemcpyAsync(w.s, sclf.data(), R * sizeof(float), cudaMemcpyHostToDevice, s);
     note_launch();
-    df_to_c64_scaled_kernel<<<sm_count() * 8, 256, 0, s>>>(rb, (const float*)w.s, Vb, vs, R);
+    df_to_c64_scaled_kernel<<<sm_count() * 8, 256, 0, s>>>(rb, (const float*)w.s, Vb, vs, R, Z);   // v_0, z_0 input
     int k = 0;
     for (int j = 0; j < m; ++j) {
-      c64* Vj = Vb + (long long)j * vs;
       c64* W1 = Vb + (long long)(j + 1) * vs;
       c64* Zj = Z + (long long)j * vs;
       cudaEventRecord(ev[0], s);
-      cudaMemcpyAsync(Zj, Vj, vs * sizeof(c64), cudaMemcpyDeviceToDevice, s);
-      p.d_u = Zj;
+      p.d_u = Zj;                                 // holds v_j: the sweep overwrites it with z_j
       st = sweep_internal(p, R, s);
       p.d_u = u_saved;
       if (st != HS_OK) break;
@@ -953,7 +955,13 @@ int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxi
         nw[r] = std::sqrt(hbuf[32 * R + r].re);
         inv[r] = (active[r] && nw[r] > 0) ? 1.0 / nw[r] : 0.0;
       }
-      B.scale(W1, inv, W1);
+      {                                           // v_{j+1}, and the next sweep's input
+        for (int r = 0; r < R; ++r) sclf[r] = (float)inv[r];
+        cudaMemcpyAsync(w.s, sclf.data(), R * sizeof(float), cudaMemcpyHostToDevice, s);
+        note_launch();
+        scale_f32_kernel<<<sm_count() * 8, 256, 0, s>>>(W1, (const float*)w.s, W1, vs, R,
+                                                        j + 1 < m ? Zj + vs : nullptr);
+      }
       cudaEventRecord(ev[3], s);
       cudaEventSynchronize(ev[3]);
       t_apply += elapsed(ev[0], ev[1]);

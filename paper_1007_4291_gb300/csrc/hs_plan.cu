@@ -254,6 +254,7 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
   if (dim == 3) return prepare_plan3d(c, omega, n, pml_width, moving_pml_width, opt_in, out);
   if (n < 3 || n % 2 != 1 || pml_width < 1 || 2 * pml_width + 1 > n) return HS_EINVAL;
   if (moving_pml_width < 1 || moving_pml_width > pml_width + 1) return HS_EINVAL;
+  if (n > 32767) return HS_EUNSUPPORTED;   // point indices are 32-bit (n^2 < 2^30)
   hs_options opt;
   hs_default_options(&opt);
   if (opt_in) opt = *opt_in;
@@ -335,6 +336,16 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
   cudaMemcpy(p->f_a2, f_a_half.data(), (n + 1) * sizeof(c64), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_pml1, pml.data(), n + 2, cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_pml2, pml.data(), n + 2, cudaMemcpyHostToDevice);
+  {   // the PML-free points form one index range [lo, hi) per axis (sigma vanishes away from the boundary)
+    int lo = 0;
+    while (lo < n && pml[lo + 1]) ++lo;
+    int hi = lo;
+    while (hi < n && !pml[hi + 1]) ++hi;
+    bool contiguous = true;
+    for (int i = hi; i < n; ++i) contiguous = contiguous && pml[i + 1];
+    p->int_lo = contiguous ? lo : 0;
+    p->int_hi = contiguous ? hi : 0;
+  }
 
   // ---- per-point omega^2/c^2 and 1/c^2 (and double-float copies)
   const size_t N2 = (size_t)n * n;
@@ -461,17 +472,25 @@ extern "C" int hs_setup(const double* c, double omega, int n, int dim, int pml_w
   return HS_OK;
 }
 
-extern "C" int hs_setup_batched(int nprob, const double* const* c, const double* omega, const int* n, int dim,
-                                int pml_width, int moving_pml_width, const hs_options* opt, void* stream,
-                                hs_plan** out) {
+namespace {
+// Batched setup with options opt_of(k) for problem k (one factor precision).
+template <typename OptOf>
+int setup_batched(int nprob, const double* const* c, const double* omega, const int* n, int dim, int pml_width,
+                  int moving_pml_width, OptOf opt_of, void* stream, hs_plan** out) {
   if (nprob < 1 || !c || !omega || !n || !out) return HS_EINVAL;
   for (int k = 0; k < nprob; ++k) out[k] = nullptr;
-  if (opt && opt->factor_prec != HS_C64 && opt->factor_prec != HS_C128) return HS_EINVAL;
+  hs_options d0;
+  hs_default_options(&d0);
+  const int prec0 = opt_of(0) ? opt_of(0)->factor_prec : d0.factor_prec;
+  for (int k = 0; k < nprob; ++k) {
+    const int pk = opt_of(k) ? opt_of(k)->factor_prec : d0.factor_prec;
+    if ((pk != HS_C64 && pk != HS_C128) || pk != prec0) return HS_EINVAL;
+  }
   std::vector<Plan*> ps;
   int st = HS_OK;
   for (int k = 0; k < nprob && st == HS_OK; ++k) {
     Plan* p = nullptr;
-    st = prepare_plan(c[k], omega[k], n[k], dim, pml_width, moving_pml_width, opt, &p);
+    st = prepare_plan(c[k], omega[k], n[k], dim, pml_width, moving_pml_width, opt_of(k), &p);
     if (st == HS_OK) ps.push_back(p);
   }
   if (st == HS_OK) st = factor_plans(ps, (cudaStream_t)stream);
@@ -481,4 +500,20 @@ extern "C" int hs_setup_batched(int nprob, const double* const* c, const double*
   }
   for (int k = 0; k < nprob; ++k) out[k] = reinterpret_cast<hs_plan*>(ps[k]);
   return HS_OK;
+}
+}  // namespace
+
+extern "C" int hs_setup_batched(int nprob, const double* const* c, const double* omega, const int* n, int dim,
+                                int pml_width, int moving_pml_width, const hs_options* opt, void* stream,
+                                hs_plan** out) {
+  return setup_batched(nprob, c, omega, n, dim, pml_width, moving_pml_width, [opt](int) { return opt; }, stream,
+                       out);
+}
+
+extern "C" int hs_setup_batched_opts(int nprob, const double* const* c, const double* omega, const int* n, int dim,
+                                     int pml_width, int moving_pml_width, const hs_options* opts, void* stream,
+                                     hs_plan** out) {
+  if (!opts) return HS_EINVAL;
+  return setup_batched(nprob, c, omega, n, dim, pml_width, moving_pml_width,
+                       [opts](int k) { return opts + k; }, stream, out);
 }

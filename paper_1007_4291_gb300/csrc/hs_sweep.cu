@@ -555,17 +555,54 @@ __global__ void __launch_bounds__(NC2 * 32 + 64) phase2_kernel(SweepArgs a) {
   __syncwarp();
   bool ok = true;
   int t = 0;
-  // y = v - Mrow * prev with Mrow the row pl of a W x W block (row stride LDP)
+  // y = v - Mrow * prev with Mrow the row pl of a W x W block (row stride
+  // LDP).  Rows start on 16-byte boundaries (W even), so both operands move
+  // two complex values per shared-memory access; the row reads of one
+  // quarter warp fall in distinct bank groups (LDP/2 is odd).
   auto row_apply = [&](C v, const C* Mrow, const C* prev) {
     C s1{0, 0}, s2{0, 0}, s3{0, 0};
 #pragma unroll
     for (int q = 0; q < W; q += 4) {
-      cfms(v, Mrow[q], prev[q]);
-      cfms(s1, Mrow[q + 1], prev[q + 1]);
-      cfms(s2, Mrow[q + 2], prev[q + 2]);
-      cfms(s3, Mrow[q + 3], prev[q + 3]);
+      C m0, m1, m2, m3, p0, p1, p2, p3;
+      ld2(Mrow + q, m0, m1);
+      ld2(Mrow + q + 2, m2, m3);
+      ld2(prev + q, p0, p1);
+      ld2(prev + q + 2, p2, p3);
+      cfms(v, m0, p0);
+      cfms(s1, m1, p1);
+      cfms(s2, m2, p2);
+      cfms(s3, m3, p3);
     }
     return cadd(cadd(v, s1), cadd(s2, s3));
+  };
+  // Gamma * ps for the symmetric Gamma (row pl read in place of column pl)
+  auto gamma_apply = [&](const C* Gm, const C* ps, C& s0, C& s1, C& s2, C& s3) {
+    const C* Grow = Gm + pl * LDP;
+#pragma unroll
+    for (int q = 0; q < W; q += 4) {
+      C g0, g1, g2, g3, p0, p1, p2, p3;
+      ld2(Grow + q, g0, g1);
+      ld2(Grow + q + 2, g2, g3);
+      ld2(ps + q, p0, p1);
+      ld2(ps + q + 2, p2, p3);
+      cfma(s0, g0, p0);
+      cfma(s1, g1, p1);
+      cfma(s2, g2, p2);
+      cfma(s3, g3, p3);
+    }
+  };
+  // s -= F^t x with F's column pl held in fcol
+  auto fcol_apply = [&](const C (&fc)[W], const C* xv, C& s0, C& s1, C& s2, C& s3) {
+#pragma unroll
+    for (int q = 0; q < W; q += 4) {
+      C x0, x1, x2, x3;
+      ld2(xv + q, x0, x1);
+      ld2(xv + q + 2, x2, x3);
+      cfms(s0, fc[q], x0);
+      cfms(s1, fc[q + 1], x1);
+      cfms(s2, fc[q + 2], x2);
+      cfms(s3, fc[q + 3], x3);
+    }
   };
   auto wait_use = [&](int u) {
     if (ok) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&fl[u % S2], (u / S2) & 1, a.spin));
@@ -610,13 +647,9 @@ __global__ void __launch_bounds__(NC2 * 32 + 64) phase2_kernel(SweepArgs a) {
       __syncwarp();
       if (lane < W) xch[lane] = v;
       __syncwarp();
-      C s0{0, 0}, s1{0, 0};
-#pragma unroll
-      for (int q = 0; q < W; q += 2) {     // Gamma_m is symmetric: lane p reads column p
-        cfma(s0, Gm[q * LDP + pl], xch[q]);
-        cfma(s1, Gm[(q + 1) * LDP + pl], xch[q + 1]);
-      }
-      const C x = cadd(s0, s1);
+      C s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
+      gamma_apply(Gm, xch, s0, s1, s2, s3);
+      const C x = cadd(cadd(s0, s1), cadd(s2, s3));
 #pragma unroll
       for (int q = 0; q < W; ++q) fcol[q] = Gm[W * LDP + q * LDP + pl];   // F_m column p
       __syncwarp();
@@ -632,22 +665,9 @@ __global__ void __launch_bounds__(NC2 * 32 + 64) phase2_kernel(SweepArgs a) {
     for (int k = m - 1; k >= 0; --k, ++t) {
       if (!wait_use(t)) break;
       const C* Gm = stage(0, t);
-      const C* ps = myrz + k * W;
       C s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
-#pragma unroll
-      for (int q = 0; q < W; q += 4) {
-        cfma(s0, Gm[q * LDP + pl], ps[q]);
-        cfma(s1, Gm[(q + 1) * LDP + pl], ps[q + 1]);
-        cfma(s2, Gm[(q + 2) * LDP + pl], ps[q + 2]);
-        cfma(s3, Gm[(q + 3) * LDP + pl], ps[q + 3]);
-      }
-#pragma unroll
-      for (int q = 0; q < W; q += 4) {   // - F_{k+1}^t x_{k+1}
-        cfms(s0, fcol[q], xch[q]);
-        cfms(s1, fcol[q + 1], xch[q + 1]);
-        cfms(s2, fcol[q + 2], xch[q + 2]);
-        cfms(s3, fcol[q + 3], xch[q + 3]);
-      }
+      gamma_apply(Gm, myrz + k * W, s0, s1, s2, s3);
+      fcol_apply(fcol, xch, s0, s1, s2, s3);   // - F_{k+1}^t x_{k+1}
       const C x = cadd(cadd(s0, s1), cadd(s2, s3));
 #pragma unroll
       for (int q = 0; q < W; ++q) fcol[q] = Gm[W * LDP + q * LDP + pl];
@@ -669,22 +689,9 @@ __global__ void __launch_bounds__(NC2 * 32 + 64) phase2_kernel(SweepArgs a) {
       for (int k = m + 1; k < K; ++k, ++t) {
         if (!wait_use(t)) break;
         const C* Gk = stage(1, t);
-        const C* ps = myrz + k * W;
         C s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
-#pragma unroll
-        for (int q = 0; q < W; q += 4) {
-          cfma(s0, Gk[q * LDP + pl], ps[q]);
-          cfma(s1, Gk[(q + 1) * LDP + pl], ps[q + 1]);
-          cfma(s2, Gk[(q + 2) * LDP + pl], ps[q + 2]);
-          cfma(s3, Gk[(q + 3) * LDP + pl], ps[q + 3]);
-        }
-#pragma unroll
-        for (int q = 0; q < W; q += 4) {   // - F'_{k-1}^t x_{k-1}
-          cfms(s0, fcol[q], xch[q]);
-          cfms(s1, fcol[q + 1], xch[q + 1]);
-          cfms(s2, fcol[q + 2], xch[q + 2]);
-          cfms(s3, fcol[q + 3], xch[q + 3]);
-        }
+        gamma_apply(Gk, myrz + k * W, s0, s1, s2, s3);
+        fcol_apply(fcol, xch, s0, s1, s2, s3);   // - F'_{k-1}^t x_{k-1}
         const C x = cadd(cadd(s0, s1), cadd(s2, s3));
 #pragma unroll
         for (int q = 0; q < W; ++q) fcol[q] = Gk[W * LDP + q * LDP + pl];

@@ -18,7 +18,7 @@ LIBPATH = os.path.join(HERE, "libhs.so")
 HS_OK, HS_EINVAL, HS_ENOMEM, HS_EBREAKDOWN, HS_ETIMEOUT, HS_ENOCONV, HS_ECUDA, HS_EUNSUPPORTED = range(8)
 HS_C64, HS_C128 = 64, 128
 
-EXPORTED = ["hs_default_options", "hs_setup", "hs_setup_batched", "hs_apply", "hs_apply_batched",
+EXPORTED = ["hs_default_options", "hs_setup", "hs_setup_batched", "hs_setup_batched_opts", "hs_apply", "hs_apply_batched",
             "hs_apply_noalloc", "hs_autotune", "hs_matvec", "hs_solve", "hs_sync", "hs_last_device_status",
             "hs_plan_bytes", "hs_release_workspace", "hs_kernel_launches", "hs_destroy", "hs_strerror",
             "hs_cnn_create", "hs_cnn_get_params", "hs_cnn_set_mode", "hs_cnn_apply", "hs_cnn_gradient",
@@ -66,6 +66,8 @@ def load(path=None):
     lib.hs_apply.argtypes = [vp, vp, vp, i, i, vp]
     lib.hs_setup_batched.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(d), ctypes.POINTER(i), i, i, i,
                                      ctypes.POINTER(HsOptions), vp, ctypes.POINTER(vp)]
+    lib.hs_setup_batched_opts.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(d), ctypes.POINTER(i), i, i, i,
+                                          ctypes.POINTER(HsOptions), vp, ctypes.POINTER(vp)]
     lib.hs_apply_batched.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(i), i, vp]
     lib.hs_autotune.argtypes = [vp, d, i, i, i, i, ctypes.POINTER(HsOptions), i, vp, ctypes.POINTER(i),
@@ -172,9 +174,16 @@ def hs_setup_batched(cs, omegas, ns, dim, pml_width, moving_pml_width, opt=None,
     om = (ctypes.c_double * k)(*[float(w) for w in omegas])
     nn = (ctypes.c_int * k)(*[int(n) for n in ns])
     out = (ctypes.c_void_p * k)()
-    o = opt if opt is not None else hs_default_options()
-    _check(lib.hs_setup_batched(k, cp, om, nn, int(dim), int(pml_width), int(moving_pml_width), ctypes.byref(o),
-                                _stream(stream), out), "hs_setup_batched")
+    if isinstance(opt, (list, tuple)):      # one options struct per problem
+        if len(opt) != k:
+            raise ValueError("one options struct per problem")
+        oa = (HsOptions * k)(*opt)
+        _check(lib.hs_setup_batched_opts(k, cp, om, nn, int(dim), int(pml_width), int(moving_pml_width), oa,
+                                         _stream(stream), out), "hs_setup_batched_opts")
+    else:
+        o = opt if opt is not None else hs_default_options()
+        _check(lib.hs_setup_batched(k, cp, om, nn, int(dim), int(pml_width), int(moving_pml_width), ctypes.byref(o),
+                                    _stream(stream), out), "hs_setup_batched")
     return [ctypes.c_void_p(out[q]) for q in range(k)]
 
 

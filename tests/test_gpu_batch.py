@@ -76,6 +76,32 @@ def test_batched_setup_matches_single_setup_and_oracle():
             hs.hs_destroy(p)
 
 
+def test_batched_setup_with_options_per_problem():
+    """Problems of different sizes reserve their own RHS capacity and chunk
+    length in one batched setup; each plan equals its own single setup."""
+    ns = [31, 63]
+    cs = [I.random_velocity(n, 300 + k) for k, n in enumerate(ns)]
+    ol = [opts(max_nrhs=2, chunk=8, graphs=0), opts(max_nrhs=6, chunk=0, graphs=0)]
+    plans = hs.hs_setup_batched([c.ravel() for c in cs], [omega_of(n) for n in ns], ns, 2, BP, BP, ol)
+    singles = [hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, o) for c, n, o in zip(cs, ns, ol)]
+    try:
+        nr = [2, 6]
+        rs = [torch.from_numpy(I.random_rhs(n, q, 60 + k)).to("cuda").to(torch.complex64)
+              for k, (n, q) in enumerate(zip(ns, nr))]
+        zs = [torch.empty_like(r) for r in rs]
+        hs.hs_apply_batched(plans, rs, zs, nr, hs.HS_C64)
+        torch.cuda.synchronize()
+        for k in range(2):
+            assert hs.hs_last_device_status(plans[k]) == hs.HS_OK
+            assert torch.equal(zs[k], apply_direct(singles[k], rs[k], nr[k])), k
+        r3 = torch.zeros(3, 31, 31, dtype=torch.complex64, device="cuda")
+        with pytest.raises(hs.HsError):          # beyond the first problem's own capacity
+            hs.hs_apply(plans[0], r3, torch.empty_like(r3), 3, hs.HS_C64)
+    finally:
+        for p in plans + singles:
+            hs.hs_destroy(p)
+
+
 def test_graph_replay_is_bit_identical_to_direct_launches():
     n = 63
     c = I.random_velocity(n, 3)

@@ -78,6 +78,32 @@ def test_matvec_matches_oracle(n, dtype, tol):
         hs.hs_destroy(plan)
 
 
+@pytest.mark.parametrize("n,bp,C", [(31, 15, C_PML),   # PML-free square of one point
+                                    (33, 4, 0.0),      # no damping: the square is the whole grid
+                                    (35, 3, C_PML)])
+@pytest.mark.parametrize("dtype,tol", [(hs.HS_C128, 1e-12), (hs.HS_C64, 2e-5)])
+def test_matvec_square_and_band_split(n, bp, C, dtype, tol):
+    """The matvec runs the PML-free square and the PML band as two kernels;
+    every point is covered once whatever the square's size."""
+    c = I.random_velocity(n, 4)
+    omega = 2 * np.pi * 2
+    o = hs.hs_default_options(pml_C=C, layers_per_step=1, max_nrhs=2)
+    plan = hs.hs_setup(c.ravel(), omega, n, 2, bp, bp, o)
+    try:
+        x = I.random_rhs(n, 2, 12)
+        tdt = torch.complex64 if dtype == hs.HS_C64 else torch.complex128
+        xg = gpu(x, tdt)
+        yg = torch.full_like(xg, float("nan"))
+        hs.hs_matvec(plan, xg, yg, 2, dtype)
+        y = yg.cpu().numpy().astype(np.complex128)
+        assert np.isfinite(y).all()
+        coef = H.stencil_coefficients(c, omega, bp, C, alpha=0.0)
+        xin = x.astype(np.complex64).astype(np.complex128) if dtype == hs.HS_C64 else x
+        assert relerr(y, H.apply_stencil(coef, xin)) <= tol
+    finally:
+        hs.hs_destroy(plan)
+
+
 # ---------------------------------------------------------------- A3-A6 apply
 
 APPLY_CASES = [

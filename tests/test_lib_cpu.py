@@ -73,9 +73,20 @@ def test_setup_rejects_bad_velocity_and_options(lib):
     assert lib.hs_setup(c.ctypes.data, 10.0, n, 4, 3, 3, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EINVAL
     # 3D: sizes are checked before the n^3 velocities are read
     assert lib.hs_setup(c.ctypes.data, 10.0, 257, 3, 3, 3, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EUNSUPPORTED
+    # 2D: point indices are 32-bit, checked before the n^2 velocities are read
+    assert lib.hs_setup(c.ctypes.data, 10.0, 32769, 2, 3, 3, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EUNSUPPORTED
     c3 = np.ones(7 ** 3)
     c3[100] = 0.0
     assert lib.hs_setup(c3.ctypes.data, 10.0, 7, 3, 2, 2, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EINVAL
     assert lib.hs_setup(None, 10.0, n, 2, 3, 3, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EINVAL
+    # batched setup with options per problem: one factor precision for all, options required
+    cs = (ctypes.c_void_p * 2)(c.ctypes.data, c.ctypes.data)
+    om = (ctypes.c_double * 2)(10.0, 10.0)
+    nn = (ctypes.c_int * 2)(n, n)
+    outs = (ctypes.c_void_p * 2)()
+    oa = (hs.HsOptions * 2)(hs.hs_default_options(), hs.hs_default_options(factor_prec=hs.HS_C128))
+    assert lib.hs_setup_batched_opts(2, cs, om, nn, 2, 3, 3, oa, None, outs) == hs.HS_EINVAL
+    assert lib.hs_setup_batched_opts(2, cs, om, nn, 2, 3, 3, None, None, outs) == hs.HS_EINVAL
+    assert not outs[0] and not outs[1]
     assert lib.hs_apply(None, None, None, 1, 64, None) == hs.HS_EINVAL
     assert lib.hs_destroy(None) == hs.HS_OK
