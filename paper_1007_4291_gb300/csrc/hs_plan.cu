@@ -246,6 +246,25 @@ static int prepare_plan3d(const double* c, double omega, int n, int pml_width, i
 // Validate the arguments, build the host tables of one problem and allocate
 // and fill its device memory (no kernel launches).  On failure nothing is
 // left allocated.
+namespace hs {
+// Per-point tables from the velocities already copied into m0: 1/c^2,
+// omega^2/c^2 in double, float and double-float (same operations and
+// rounding as a host loop would do, so the tables are exact copies).
+__global__ void point_tables_kernel(double* m0, double* cinv2, float* fm0, float* km0, long long N, double omega2) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (long long)gridDim.x * blockDim.x) {
+    const double cv = m0[k];
+    const double ci = 1.0 / (cv * cv);
+    const double m = omega2 * ci;
+    const float hi = (float)m;
+    cinv2[k] = ci;
+    m0[k] = m;
+    fm0[k] = hi;
+    km0[2 * k] = hi;
+    km0[2 * k + 1] = (float)(m - (double)hi);
+  }
+}
+}  // namespace hs
+
 static int prepare_plan(const double* c, double omega, int n, int dim, int pml_width, int moving_pml_width,
                         const hs_options* opt_in, Plan** out) {
   *out = nullptr;
@@ -354,14 +373,6 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
       o[0] = (float)x;
       o[1] = (float)(x - (double)o[0]);
     };
-    std::vector<double> m0(N2), ci2(N2);
-    std::vector<float> fm0(N2), km0(2 * N2);
-    for (size_t k = 0; k < N2; ++k) {
-      ci2[k] = 1.0 / (c[k] * c[k]);
-      m0[k] = omega * omega * ci2[k];
-      fm0[k] = (float)m0[k];
-      split(m0[k], &km0[2 * k]);
-    }
     std::vector<float> kis(4 * (n + 2)), ka(4 * (n + 1));
     for (int k = 0; k <= n + 1; ++k) { split(inv_s[k].re, &kis[4 * k]); split(inv_s[k].im, &kis[4 * k + 2]); }
     for (int k = 0; k <= n; ++k) { split(a_half[k].re, &ka[4 * k]); split(a_half[k].im, &ka[4 * k + 2]); }
@@ -370,10 +381,11 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
         (st = dalloc(*p, (float**)&p->k_inv_s2, 4 * (n + 2))) || (st = dalloc(*p, (float**)&p->k_a1, 4 * (n + 1))) ||
         (st = dalloc(*p, (float**)&p->k_a2, 4 * (n + 1))))
       return fail(st);
-    cudaMemcpy(p->d_m0, m0.data(), N2 * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(p->f_m0, fm0.data(), N2 * sizeof(float), cudaMemcpyHostToDevice);
-    cudaMemcpy(p->d_cinv2, ci2.data(), N2 * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(p->k_m0, km0.data(), 2 * N2 * sizeof(float), cudaMemcpyHostToDevice);
+    // velocities to the device once; the per-point tables are formed there
+    cudaMemcpy(p->d_m0, c, N2 * sizeof(double), cudaMemcpyHostToDevice);
+    const long long gb = std::min<long long>(((long long)N2 + 255) / 256, 4096);
+    hs::point_tables_kernel<<<(int)gb, 256>>>(p->d_m0, p->d_cinv2, p->f_m0, (float*)p->k_m0, (long long)N2, omega * omega);
+    if (cudaStreamSynchronize(0) != cudaSuccess) return fail(HS_ECUDA);
     cudaMemcpy(p->k_inv_s1, kis.data(), kis.size() * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(p->k_inv_s2, kis.data(), kis.size() * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(p->k_a1, ka.data(), ka.size() * sizeof(float), cudaMemcpyHostToDevice);

@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase1_kernel(SweepA
 // The two warps of a RHS meet twice on a named barrier (psi'_{m+1}, then
 // x_m); each half has its own producer warp streaming the separator factors
 // through an S2-deep TMA ring in the order its chain uses them.
-constexpr int WPC = 4;           // RHS per CTA in phase 2
+constexpr int WPC = 1;           // RHS per CTA in phase 2 (one CTA per RHS and front: the chains run on otherwise idle SMs)
 constexpr int NC2 = 2 * WPC;     // consumer warps (top and bottom per RHS)
 // TMA ring depth: 4 stages per half, 2 when the separator factors are large
 template <typename R, int W> struct Ring2 {
