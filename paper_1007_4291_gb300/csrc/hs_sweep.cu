@@ -454,17 +454,31 @@ __global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase1_kernel(SweepA
 // The two warps of a RHS meet twice on a named barrier (psi'_{m+1}, then
 // x_m); each half has its own producer warp streaming the separator factors
 // through an S2-deep TMA ring in the order its chain uses them.
-constexpr int WPC = 1;           // RHS per CTA in phase 2 (one CTA per RHS and front: the chains run on otherwise idle SMs)
-constexpr int NC2 = 2 * WPC;     // consumer warps (top and bottom per RHS)
+// RHS per CTA (wpc, from the block size): one while the RHS of both fronts
+// fit on the SMs one CTA each (the chain warps then have a scheduler each,
+// on SMs the chunk phases leave idle), else two or four so that the
+// separator solve stays within one wave.
+constexpr int WPC_MAX = 4;
 // TMA ring depth: 4 stages per half, 2 when the separator factors are large
 template <typename R, int W> struct Ring2 {
   static constexpr int S = (8LL * 3 * W * (W + 2) * 2 * (long long)sizeof(R) <= 128 * 1024) ? 4 : 2;
 };
 
 template <typename R, int W>
-size_t phase2_smem(int nsep) {
+size_t phase2_smem(int nsep, int wpc = WPC_MAX) {
   return 256 + (size_t)2 * Ring2<R, W>::S * round128((size_t)red_elems(W) * sizeof(cplx<R>)) +
-         (size_t)WPC * (nsep + 3) * W * sizeof(cplx<R>);
+         (size_t)wpc * (nsep + 3) * W * sizeof(cplx<R>);
+}
+int phase2_wpc(int R, int nfront) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  int wpc = 1;
+  while (wpc < WPC_MAX && (long long)((R + wpc - 1) / wpc) * nfront > sms) wpc *= 2;
+  return wpc;
 }
 
 // Named barrier of the two warps of one RHS, returning the AND of `v`.
@@ -482,7 +496,7 @@ __device__ __forceinline__ bool pair_barrier_and(int id, bool v) {
 }
 
 template <typename R, int W>
-__global__ void __launch_bounds__(NC2 * 32 + 64) phase2_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(2 * WPC_MAX * 32 + 64) phase2_kernel(SweepArgs a) {
   using C = cplx<R>;
   constexpr int LDP = W + 2;
   constexpr int S2 = Ring2<R, W>::S;
@@ -499,6 +513,7 @@ __global__ void __launch_bounds__(NC2 * 32 + 64) phase2_kernel(SweepArgs a) {
   C* rz = reinterpret_cast<C*>(smem_raw + 256 + (size_t)2 * S2 * sstride);
   const C* red = reinterpret_cast<const C*>(a.red) + d.red_off;
   const int tid = threadIdx.x;
+  const int wpc = ((int)blockDim.x - 64) / 64;   // RHS per CTA (two consumer warps each)
   auto stage = [&](int h, int u) { return reinterpret_cast<C*>(smem_raw + 256 + (size_t)(h * S2 + u % S2) * sstride); };
   // separator of use u of half h
   auto slot_of = [&](int h, int u) {
@@ -509,13 +524,13 @@ __global__ void __launch_bounds__(NC2 * 32 + 64) phase2_kernel(SweepArgs a) {
   if (tid == 0) {
     for (int u = 0; u < 2 * S2; ++u) {
       mbar_init(&full[u], 1);
-      mbar_init(&empty[u], WPC);
+      mbar_init(&empty[u], wpc);
     }
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid >= NC2 * 32) {
-    const int h = (tid - NC2 * 32) >> 5;
+  if (tid >= 2 * wpc * 32) {
+    const int h = (tid - 2 * wpc * 32) >> 5;
     if ((tid & 31) == 0 && nuse[h] > 0)
       ring_producer(full + h * S2, empty + h * S2, S2, nuse[h], a.spin, a.status, front, [&](int t) {
         mbar_arrive_expect_tx(&full[h * S2 + t % S2], rbytes);
@@ -524,8 +539,8 @@ __global__ void __launch_bounds__(NC2 * 32 + 64) phase2_kernel(SweepArgs a) {
     return;
   }
   const int lane = tid & 31, wq = tid >> 5;
-  const int rhs = wq & (WPC - 1), half = wq / WPC;
-  const int r = blockIdx.y * WPC + rhs;
+  const int rhs = wq % wpc, half = wq / wpc;
+  const int r = blockIdx.y * wpc + rhs;
   const bool valid = r < a.R;
   const int rr = valid ? r : (a.R - 1);
   const int pl = lane < W ? lane : 0;
@@ -923,14 +938,15 @@ int run_stage_w(const Plan& p, SweepArgs a, cudaStream_t s) {
   const size_t sm1 = tile_smem<R, W>(dmax, false);
   const size_t sm3 = tile_smem<R, W>(dmax, true);
   set_attrs_w<R, W>();
-  if (sm1 > 220 * 1024 || sm3 > 220 * 1024 || phase2_smem<R, W>(a.P - 1) > 220 * 1024) return HS_EUNSUPPORTED;
+  const int wpc = phase2_wpc(a.R, a.nfront);
+  if (sm1 > 220 * 1024 || sm3 > 220 * 1024 || phase2_smem<R, W>(a.P - 1, wpc) > 220 * 1024) return HS_EUNSUPPORTED;
   dim3 g13(a.P, (a.R + TL::RG - 1) / TL::RG, a.nfront);
   note_launch();
   phase1_kernel<R, W><<<g13, TL::NCONS + 32, sm1, s>>>(a);
   if (a.P > 1) {
-    dim3 g2(1, (a.R + WPC - 1) / WPC, a.nfront);
+    dim3 g2(1, (a.R + wpc - 1) / wpc, a.nfront);
     note_launch();
-    phase2_kernel<R, W><<<g2, NC2 * 32 + 64, phase2_smem<R, W>(a.P - 1), s>>>(a);
+    phase2_kernel<R, W><<<g2, 2 * wpc * 32 + 64, phase2_smem<R, W>(a.P - 1, wpc), s>>>(a);
   }
   note_launch();
   phase3_kernel<R, W><<<g13, TL::NCONS + 32, sm3, s>>>(a);

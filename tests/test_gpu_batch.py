@@ -102,6 +102,24 @@ def test_batched_setup_with_options_per_problem():
             hs.hs_destroy(p)
 
 
+@pytest.mark.parametrize("nrhs", [100, 160])     # two and four RHS per separator-solve CTA
+def test_many_rhs_match_the_same_rhs_in_slices(nrhs):
+    """The separator solve groups more RHS per CTA when the RHS of both
+    fronts outnumber the SMs; each RHS's arithmetic is unchanged, so the
+    result equals the applications of 50-RHS slices (one RHS per CTA)."""
+    n = 63
+    c = I.random_velocity(n, 11)
+    p = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(max_nrhs=nrhs, graphs=0))
+    try:
+        r = torch.from_numpy(I.random_rhs(n, nrhs, 13)).to("cuda").to(torch.complex64)
+        z = apply_direct(p, r, nrhs)
+        for q0 in range(0, nrhs, 50):
+            q1 = min(nrhs, q0 + 50)
+            assert torch.equal(z[q0:q1], apply_direct(p, r[q0:q1].contiguous(), q1 - q0)), q0
+    finally:
+        hs.hs_destroy(p)
+
+
 def test_graph_replay_is_bit_identical_to_direct_launches():
     n = 63
     c = I.random_velocity(n, 3)
