@@ -467,10 +467,15 @@ def run_ours(args):
         f_host = torch.from_numpy(wl["f"]).pin_memory()
         u_host = torch.empty_like(f_host).pin_memory()
 
+        copy_stream = torch.cuda.Stream()
+
         def step_e2e():
-            f_dev.copy_(f_host, non_blocking=True)
+            # the right-hand sides upload on a side stream while the setup runs
+            with torch.cuda.stream(copy_stream):
+                f_dev.copy_(f_host, non_blocking=True)
             plan = hs.hs_setup(c_host, wl["omega"], n, 2, wl["bp"], wl["b"], opt, stream)
             u_dev.zero_()
+            stream.wait_stream(copy_stream)
             code, info = hs.hs_solve(plan, f_dev, u_dev, R, args.tol, 400, stream)
             hs.hs_destroy(plan)
             u_host.copy_(u_dev, non_blocking=True)
