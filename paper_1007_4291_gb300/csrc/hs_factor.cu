@@ -112,16 +112,27 @@ __device__ bool invert_inplace(cplx<R>* A, int* piv, int lane) {
   constexpr int LD = W + 1;
   bool ok = true;
   for (int k = 0; k < W; ++k) {
-    R v = (lane < W && lane >= k) ? cabs2(A[lane * LD + k]) : R(-1);
-    int idx = lane;
+    int pr;
+    if constexpr (sizeof(R) == 4) {
+      // |a|^2 >= 0 orders like its bit pattern: one warp max-reduction, then
+      // the lowest lane holding the maximum (ties as in a scan from row k)
+      const unsigned key = (lane < W && lane >= k) ? __float_as_uint(cabs2(A[lane * LD + k])) + 1u : 0u;
+      const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+      pr = __ffs(__ballot_sync(0xffffffffu, key == kmax)) - 1;
+      const float v = __uint_as_float(kmax - 1u);
+      if (!(v > 0.f) || !isfinite(v)) ok = false;
+    } else {
+      R v = (lane < W && lane >= k) ? cabs2(A[lane * LD + k]) : R(-1);
+      int idx = lane;
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) {
-      R ov = Shfl<R>::xr(v, m);
-      int oi = __shfl_xor_sync(0xffffffffu, idx, m);
-      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+      for (int m = 16; m > 0; m >>= 1) {
+        R ov = Shfl<R>::xr(v, m);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, m);
+        if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+      }
+      if (!(v > R(0)) || !isfinite(v)) ok = false;
+      pr = idx;
     }
-    if (!(v > R(0)) || !isfinite(v)) ok = false;
-    const int pr = idx;
     if (lane == 0) piv[k] = pr;
     if (pr != k && lane < W) {
       cplx<R> t = A[k * LD + lane];
@@ -139,13 +150,11 @@ __device__ bool invert_inplace(cplx<R>* A, int* piv, int lane) {
     }
     __syncwarp();
     if (lane < W && lane != k) {
+      // every column, k included (row[k] is then replaced by -f pinv)
       cplx<R>* row = A + lane * LD;
       const cplx<R>* prow = A + k * LD;
-#pragma unroll 4
-      for (int q = 0; q < W; ++q) {
-        if (q == k) continue;
-        cfms(row[q], f, prow[q]);
-      }
+#pragma unroll
+      for (int q = 0; q < W; ++q) cfms(row[q], f, prow[q]);
       row[k] = cmul(cplx<R>{-f.re, -f.im}, pinv);
     }
     __syncwarp();

@@ -190,6 +190,24 @@ def test_autotune_writes_cache_that_setup_reads(tmp_path):
     os.remove(cache)
 
 
+@pytest.mark.parametrize("prec", [hs.HS_C64, hs.HS_C128])
+def test_non_finite_pivot_is_reported_as_breakdown(prec):
+    """omega = 1e160 overflows omega^2/c^2 in both factor precisions: every
+    diagonal block has a non-finite pivot, the setup reports HS_EBREAKDOWN
+    (no plan is returned), and the next setup still runs."""
+    n = 31
+    c = I.constant_velocity(n)
+    with pytest.raises(hs.HsError) as err:
+        hs.hs_setup(c.ravel(), 1e160, n, 2, BP, BP, opts(factor_prec=prec))
+    assert err.value.code == hs.HS_EBREAKDOWN
+    good = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(factor_prec=prec))
+    try:
+        r = torch.from_numpy(I.random_rhs(n, 2, 5)).to("cuda").to(torch.complex64)
+        apply_direct(good, r, 2)
+    finally:
+        hs.hs_destroy(good)
+
+
 def test_expired_device_wait_is_reported_and_context_stays_usable():
     """A plan whose device waits may take one clock cycle: the first
     shared-memory copy cannot land in time, every CTA gives up together,
