@@ -17,10 +17,12 @@
 //   phase 3, per chunk in parallel: x_j = z_j - G_j C_j x_{j+1} from the
 //            right separator, plus the left-spike correction -W_j C_{l-1} x_sep
 //            on the output rows.
-// Threads: T lanes share one right-hand side and split the W window rows;
-// full vectors are exchanged by warp shuffles.  Per-column factor payloads
-// (G_j | W_j rows | c_j) are double-buffered into shared memory with 1D TMA
-// bulk copies completed on mbarriers (bounded waits -> HS_ETIMEOUT).
+// Phases 1 and 3: each consumer thread owns a few window rows of two RHS;
+// the vector carried from column to column goes through shared memory, one
+// named barrier per column.  Per-column factor payloads (G_j | W_j rows |
+// c_j) stream into a shared-memory ring with 1D TMA bulk copies completed on
+// mbarriers (bounded waits -> HS_ETIMEOUT).  Phase 2: one or a few RHS per
+// CTA, two chain warps per RHS (see below).
 #include <algorithm>
 #include "hs_internal.cuh"
 #include "hs_device.cuh"
@@ -28,8 +30,6 @@
 
 namespace hs {
 namespace {
-
-constexpr int NT = 128;  // threads per CTA of the chunk kernels
 
 struct SweepArgs {
   int n, L, P, R, mode, nfront;
@@ -48,21 +48,7 @@ struct SweepArgs {
   long long spin;
 };
 
-template <int W> struct TPR { static constexpr int value = (W >= 24) ? 8 : 4; };
-
-// Gather the full W-vector from the T lanes of this RHS (each owns ROWS rows).
-template <typename R, int W, int T>
-__device__ __forceinline__ void allgather(const cplx<R> (&own)[W / T], cplx<R> (&full)[W]) {
-  constexpr int ROWS = W / T;
-#pragma unroll
-  for (int s = 0; s < T; ++s) {
-#pragma unroll
-    for (int q = 0; q < ROWS; ++q) full[s * ROWS + q] = shfl_c(own[q], s, T);
-  }
-}
-
 constexpr int S13 = 4;        // TMA ring depth of the chunk kernels (phases 1 and 3)
-constexpr int NCW = NT / 32;  // consumer warps per CTA; one more warp produces the ring
 
 __host__ __device__ __forceinline__ size_t round128(size_t b) { return (b + 127) / 128 * 128; }
 
@@ -134,17 +120,6 @@ struct RhsTerms {
     }
   }
 };
-
-// Shared-memory bytes of the chunk kernels: barriers, S13 ring stages each
-// holding the column payload and (phase 3) this CTA's tile of the z store,
-// and (phase 3) the left-separator vectors of the CTA's RHS.
-template <typename R, int W, int T>
-size_t chunk_smem(int d_out, bool p3) {
-  const size_t pb = round128((size_t)payload_elems(W, d_out) * sizeof(cplx<R>));
-  const size_t zb = p3 ? round128((size_t)(NT / T) * W * sizeof(cplx<R>)) : 0;
-  const size_t bb = p3 ? round128((size_t)(NT / T) * W * sizeof(cplx<R>)) : 0;
-  return 256 + S13 * (pb + zb) + bb;
-}
 
 // Producer warp of a ring: issues use t of nuses into stage t % S once the
 // consumers have released use t - S.  Returns after every copy it issued has
