@@ -66,9 +66,9 @@ typedef struct {
                             sweeps a different Krylov vector at every step and launches directly. default 1 */
   int krylov_basis;      /* 2D complex64 plans: 0 FGMRES with a double-float Arnoldi basis; 1 mixed-
                             precision refinement: cycles of FGMRES with an FP32 basis (FP32
-                            Gram-Schmidt) restarted from the double-float true residual, x
-                            updated in double-float (a network attached with hs_attach_cnn
-                            uses mode 0).                                                    default 1 */
+                            products A z_j and Gram-Schmidt) restarted from the double-float
+                            true residual, x updated in double-float (a network attached with
+                            hs_attach_cnn uses mode 0).                                      default 1 */
   double inner_tol;      /* refinement cycles end when their residual estimate has fallen by this
                             factor (or below tol).                                             default 1e-4 */
   int frontal_gemm;      /* 3D setup, frontal Schur updates of complex64 factors: 0 CUDA-core FP32

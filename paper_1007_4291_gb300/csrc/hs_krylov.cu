@@ -849,9 +849,10 @@ int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs
 
 // Mixed-precision refinement (2D, complex64 factors): each cycle restarts
 // from the true residual r = f - A x computed in double-float and runs
-// FGMRES with an FP32 Arnoldi basis (complex64 vectors, FP32 Gram-Schmidt,
-// the products A z_j still in double-float) until its Givens estimate has
-// fallen by inner_tol (or reaches tol ||f||); x is updated in double-float.
+// FGMRES with an FP32 Arnoldi basis (complex64 vectors, FP32 products A z_j,
+// FP32 Gram-Schmidt) until its Givens estimate has fallen by inner_tol (or
+// reaches tol ||f||); the cycle's correction is formed in FP32 and added to
+// the double-float iterate.
 // FP64-class arithmetic is kept exactly where the iterate and the residual
 // that decides convergence are formed.
 int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs_solve_info* info,
