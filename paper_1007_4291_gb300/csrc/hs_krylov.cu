@@ -696,19 +696,19 @@ int solve_t(Plan& p, const void* f, void* u, int nrhs, double tol, int maxit, hs
       V* Vj = Vb + (long long)j * vs;
       V* W1 = Vb + (long long)(j + 1) * vs;
       // z_j = M_alpha v_j in the factor precision, computed in place in Z_j
+      // (2D: z_j moves with j, direct launches).  3D vectors are small and
+      // the slab sweep is many short launches: the sweep runs on the plan's
+      // own vector as a replayed CUDA graph and z_j is copied out.
       cudaEventRecord(ev[0], s);
-      if (p.prec == HS_C64) {
-        c64* Zj = Z + (long long)j * vs;
-        K.to_c64(Vj, Zj);
-        p.d_u = Zj;
-      } else {
-        c128* Zj2 = Z2 + (long long)j * vs;
-        cudaMemcpyAsync(Zj2, Vj, vs * sizeof(c128), cudaMemcpyDeviceToDevice, s);
-        p.d_u = Zj2;
-      }
-      st = sweep_internal(p, R, s);   // z_j moves with j: direct launches
-      void* zj = p.d_u;
+      const bool g3 = p.dim == 3 && p.opt.graphs != 0;
+      void* zj = (p.prec == HS_C64) ? (void*)(Z + (long long)j * vs) : (void*)(Z2 + (long long)j * vs);
+      void* work = g3 ? u_saved : zj;
+      if (p.prec == HS_C64) K.to_c64(Vj, (c64*)work);
+      else cudaMemcpyAsync(work, Vj, vs * sizeof(c128), cudaMemcpyDeviceToDevice, s);
+      p.d_u = work;
+      st = sweep_internal(p, R, s, g3);
       p.d_u = u_saved;
+      if (st == HS_OK && g3) cudaMemcpyAsync(zj, work, vs * zes, cudaMemcpyDeviceToDevice, s);
       if (st == HS_OK && cnn_on) {      // correction c = s N(z_j / s) of the sweep output
         cudaMemsetAsync(K.w.C, 0, vs * zes, s);
         st = cnn_correct(*net, zj, K.w.C, p.prec, R, p.n, s);

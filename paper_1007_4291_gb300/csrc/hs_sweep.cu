@@ -1068,8 +1068,8 @@ struct SweepGraphs {
 }  // namespace
 
 int sweep_internal(Plan& p, int nrhs, cudaStream_t s, bool graph) {
-  if (p.dim == 3) return sweep3(p, nrhs, s);
-  if (!graph) return sweep_launch(p, nrhs, s);
+  auto launch = [&p, nrhs](cudaStream_t c) -> int { return p.dim == 3 ? sweep3(p, nrhs, c) : sweep_launch(p, nrhs, c); };
+  if (!graph) return launch(s);
   if (!p.graphs) p.graphs = new SweepGraphs();
   SweepGraphs& gs = *static_cast<SweepGraphs*>(p.graphs);
   std::lock_guard<std::mutex> lock(gs.m);
@@ -1081,12 +1081,12 @@ int sweep_internal(Plan& p, int nrhs, cudaStream_t s, bool graph) {
       return ce == cudaSuccess ? HS_OK : cuda_status(ce);
     }
   }
-  sweep_prepare_attributes(p.prec);
+  if (p.dim == 2) sweep_prepare_attributes(p.prec);
   if (!gs.cap) HS_CUDA_TRY(cudaStreamCreateWithFlags(&gs.cap, cudaStreamNonBlocking));
   SweepGraphs::Entry e{};
   e.nrhs = nrhs;
   std::copy(ptrs, ptrs + 6, e.ptrs);
-  int st = capture_graph(gs.cap, [&](cudaStream_t c) -> int { return sweep_launch(p, nrhs, c); }, &e.exec, &e.kernels);
+  int st = capture_graph(gs.cap, launch, &e.exec, &e.kernels);
   if (st != HS_OK) return st;
   gs.list.push_back(e);
   note_launch(e.kernels);
