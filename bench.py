@@ -178,7 +178,7 @@ def oracle_sample(wl, nrhs, iters, budget_s=20.0):
     t0 = time.perf_counter()
     for blk in lower[1:]:
         ta = time.perf_counter()
-        fb = S.factor_block(blk, wl["c"], wl["omega"], bp, b, wl["C"], wl["alpha"])
+        fb = S.factor_block(blk, wl["c"], wl["omega"], bp, b, wl["C"], wl["alpha"], Cm=2.0 * wl["C"])
         tb = time.perf_counter()
         fb.t_tilde(r[:, blk.lo - 1:blk.hi, :])
         tc = time.perf_counter()
@@ -214,7 +214,10 @@ def run_reference(args):
     if rank != 0:
         return
     wl = workload(args)
-    iters = 12
+    # FGMRES iterations of the method on this workload with the default
+    # moving-PML strength 2C (the GPU solve and the oracle agree on the
+    # iteration count wherever the oracle can run whole solves)
+    iters = 9
     vals = []
     for _ in range(args.warmup):
         oracle_sample(wl, args.nrhs, iters, budget_s=5.0)
