@@ -3,14 +3,16 @@
 
 One step = the whole hot path on one batch: hs_setup (batched factorisation
 of every moving-PML subproblem) + hs_solve (FGMRES to relative residual
-1e-6 with the two-front sweep as preconditioner, FP64 matvec and
-Gram-Schmidt) for 64 right-hand sides on the 2D n = 2047 grid
-(omega/2pi = 128, 16 points per wavelength), synthetic seeded inputs.
+1e-6 with the two-front sweep as preconditioner: refinement cycles with an
+FP32 Arnoldi basis restarted from the double-float true residual) for 64
+right-hand sides on the 2D n = 2047 grid (omega/2pi = 128, 16 points per
+wavelength), synthetic seeded inputs.
 
 Prints one JSON line (rank 0).  `value` = right-hand sides solved to 1e-6
 per second (whole job, all GPUs), with f resident on the device; `e2e` is the
-same through the C ABI with host buffers (f copied in, u copied out, c read
-from host by hs_setup) inside the timed region.  `--impl reference` times the
+same through the C ABI with host buffers (f copied in on a side stream
+during the setup, u copied out, c read from host by hs_setup) inside the
+timed region.  `--impl reference` times the
 complex128 CPU oracle on a bounded sample of the same workload.
 """
 import argparse
