@@ -62,8 +62,10 @@ typedef struct {
   int reorth;            /* 0: classical Gram-Schmidt; 1: CGS with a second pass when needed (DGKS).  default 0 */
   long long spin_budget; /* SM clock cycles a device-side barrier wait may take before HS_ETIMEOUT.   default 1<<30 */
   int graphs;            /* 1: hs_apply replays the stage chain of the sweep as a CUDA graph
-                            (captured on first use per nrhs); 0: direct launches.  hs_solve
-                            sweeps a different Krylov vector at every step and launches directly. default 1 */
+                            (captured on first use per nrhs); 0: direct launches.  hs_solve on a
+                            2D plan sweeps a different Krylov vector at every step and launches
+                            directly; on a 3D plan it replays the graph on the plan's own vector
+                            and copies the result out.                                      default 1 */
   int krylov_basis;      /* 2D complex64 plans: 0 FGMRES with a double-float Arnoldi basis; 1 mixed-
                             precision refinement: cycles of FGMRES with an FP32 basis (FP32
                             products A z_j and Gram-Schmidt) restarted from the double-float
