@@ -76,9 +76,13 @@ typedef struct {
   int frontal_gemm;      /* 3D setup, frontal Schur updates of complex64 factors: 0 CUDA-core FP32
                             FMA, 1 TF32 tensor cores (one pass), 3 3xTF32 tensor cores (split
                             operands, FP32-level accuracy).  Complex128 factors use FP64 FMA.   default 3 */
-  const char* tune_cache;/* path of the chunk-length table written by hs_autotune; with chunk = 0,
-                            hs_setup takes the chunk length from it when it holds the problem's
-                            key.  NULL: not used.  The string must outlive the hs_setup call.    default NULL */
+  const char* tune_cache;/* path of the table written by hs_autotune; with chunk = 0, hs_setup
+                            takes the chunk length (and, with sep_rhs_per_cta = 0, the separator
+                            grouping) from it when it holds the problem's key.  NULL: not used.
+                            The string must outlive the hs_setup call.                        default NULL */
+  int sep_rhs_per_cta;   /* RHS per CTA of the separator solve (phase 2 of every sweep stage):
+                            0 picks one while the RHS of both fronts fit on the SMs one CTA each,
+                            else two or four; 1, 2 or 4 fix it.                               default 0 */
 } hs_options;
 
 typedef struct hs_plan hs_plan;
@@ -195,18 +199,20 @@ int hs_apply_batched(int nprob, hs_plan* const* plans, const void* const* r, voi
                      int dtype, void* stream);
 
 /*
- * hs_autotune -- pick the x1 chunk length of the subproblem solves (the
- * chunk count sets the CTAs per front of every sweep stage) for one problem
- * shape by timing: for each candidate length it sets up the problem and times
- * hs_apply of nrhs RHS with CUDA events on `stream`.  Writes the fastest
- * length to *best_chunk (and its time per application in ms to *best_ms when
- * not NULL).  When opt->tune_cache is set, appends the result to that text
- * file under the key (n, pml_width, moving_pml_width, layers_per_step,
- * factor_prec, nrhs), which later hs_setup calls with chunk = 0 and
- * max_nrhs = nrhs read.  c is a HOST pointer as in hs_setup.
+ * hs_autotune -- pick the tile shape of the sweep for one problem shape by
+ * timing: the x1 chunk length of the subproblem solves (the chunk count sets
+ * the CTAs per front of every sweep stage) and the RHS per CTA of the
+ * separator solve (1, 2 or 4).  For each candidate length it sets up the
+ * problem and, for each grouping, times hs_apply of nrhs RHS with CUDA events
+ * on `stream`.  Writes the fastest pair to *best_chunk and *best_sep (when not
+ * NULL) and its time per application in ms to *best_ms (when not NULL).
+ * When opt->tune_cache is set, appends the result to that text file under the
+ * key (n, pml_width, moving_pml_width, layers_per_step, factor_prec, nrhs),
+ * which later hs_setup calls with chunk = 0 and max_nrhs = nrhs read.  c is a
+ * HOST pointer as in hs_setup.  2D plans only (HS_EUNSUPPORTED for dim 3).
  */
 int hs_autotune(const double* c, double omega, int n, int dim, int pml_width, int moving_pml_width,
-                const hs_options* opt, int nrhs, void* stream, int* best_chunk, double* best_ms);
+                const hs_options* opt, int nrhs, void* stream, int* best_chunk, double* best_ms, int* best_sep);
 
 /*
  * hs_matvec -- y = A x with the Eq. helmd operator (alpha = 0).

@@ -44,20 +44,31 @@ void forget_batch_graphs(long long uid) {
   }
 }
 
-// Chunk length recorded by hs_autotune for this key, or 0.
-int tuned_chunk(const char* path, int n, int bp, int b, int dL, int prec, int nrhs) {
+// Chunk length (and separator grouping, 0 when the entry has none) recorded
+// by hs_autotune for this key, or 0.
+int tuned_chunk(const char* path, int n, int bp, int b, int dL, int prec, int nrhs, int* sep) {
+  *sep = 0;
   if (!path) return 0;
   FILE* f = std::fopen(path, "r");
   if (!f) return 0;
   char line[256];
   int best = 0;
   while (std::fgets(line, sizeof(line), f)) {
-    int kn, kbp, kb, kdl, kp, kr, chunk;
+    int kn, kbp, kb, kdl, kp, kr, chunk, ks = 0;
     double ms;
-    if (std::sscanf(line, "2d n=%d bp=%d b=%d d=%d prec=%d nrhs=%d chunk=%d ms=%lf", &kn, &kbp, &kb, &kdl, &kp,
-                    &kr, &chunk, &ms) == 8 &&
-        kn == n && kbp == bp && kb == b && kdl == dL && kp == prec && kr == nrhs && chunk >= 2)
+    const int got = std::sscanf(line, "2d n=%d bp=%d b=%d d=%d prec=%d nrhs=%d chunk=%d sep=%d ms=%lf", &kn, &kbp,
+                                &kb, &kdl, &kp, &kr, &chunk, &ks, &ms);
+    if (got != 9) {     // entries without a separator grouping
+      ks = 0;
+      if (std::sscanf(line, "2d n=%d bp=%d b=%d d=%d prec=%d nrhs=%d chunk=%d ms=%lf", &kn, &kbp, &kb, &kdl, &kp,
+                      &kr, &chunk, &ms) != 8)
+        continue;
+    }
+    if (kn == n && kbp == bp && kb == b && kdl == dL && kp == prec && kr == nrhs && chunk >= 2 &&
+        (ks == 0 || ks == 1 || ks == 2 || ks == 4)) {
       best = chunk;  // the last entry for a key wins
+      *sep = ks;
+    }
   }
   std::fclose(f);
   return best;
@@ -142,9 +153,12 @@ extern "C" int hs_apply_batched(int nprob, hs_plan* const* plans, const void* co
 }
 
 extern "C" int hs_autotune(const double* c, double omega, int n, int dim, int pml_width, int moving_pml_width,
-                           const hs_options* opt_in, int nrhs, void* stream, int* best_chunk, double* best_ms) {
+                           const hs_options* opt_in, int nrhs, void* stream, int* best_chunk, double* best_ms,
+                           int* best_sep) {
   if (!best_chunk || nrhs < 1) return HS_EINVAL;
+  if (dim != 2) return HS_EUNSUPPORTED;
   *best_chunk = 0;
+  int bsep = 0;
   hs_options opt;
   hs_default_options(&opt);
   if (opt_in) opt = *opt_in;
@@ -182,20 +196,28 @@ extern "C" int hs_autotune(const double* c, double omega, int n, int dim, int pm
     if (s2 == HS_EUNSUPPORTED) continue;  // e.g. separator chain too long for this length
     if (s2 != HS_OK) { st = s2; break; }
     const int dtype = opt.factor_prec;
-    s2 = hs_apply(plan, buf, buf, nrhs, dtype, stream);  // warm-up (and graph capture)
-    const int reps = 3;
-    cudaEventRecord(e0, s);
-    for (int k = 0; k < reps && s2 == HS_OK; ++k) s2 = hs_apply(plan, buf, buf, nrhs, dtype, stream);
-    cudaEventRecord(e1, s);
-    cudaError_t ce = cudaEventSynchronize(e1);
-    if (s2 == HS_OK && ce != cudaSuccess) s2 = cuda_status(ce);
-    if (s2 == HS_OK) s2 = hs_last_device_status(plan);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    Plan& pp = *reinterpret_cast<Plan*>(plan);
+    for (int sep : {1, 2, 4}) {
+      // a new grouping changes the launches: the sweep graph is captured anew
+      cudaStreamSynchronize(s);
+      release_sweep_graphs(pp);
+      pp.opt.sep_rhs_per_cta = sep;
+      s2 = hs_apply(plan, buf, buf, nrhs, dtype, stream);  // warm-up (and graph capture)
+      const int reps = 3;
+      cudaEventRecord(e0, s);
+      for (int k = 0; k < reps && s2 == HS_OK; ++k) s2 = hs_apply(plan, buf, buf, nrhs, dtype, stream);
+      cudaEventRecord(e1, s);
+      cudaError_t ce = cudaEventSynchronize(e1);
+      if (s2 == HS_OK && ce != cudaSuccess) s2 = cuda_status(ce);
+      if (s2 == HS_OK) s2 = hs_last_device_status(plan);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (s2 == HS_EUNSUPPORTED) { s2 = HS_OK; continue; }  // this length and grouping do not fit
+      if (s2 != HS_OK) break;
+      if (ms / reps < best) { best = ms / reps; *best_chunk = L; bsep = sep; }
+    }
     hs_destroy(plan);
-    if (s2 == HS_EUNSUPPORTED) continue;  // the separator chain of this length does not fit
     if (s2 != HS_OK) { st = s2; break; }
-    if (ms / reps < best) { best = ms / reps; *best_chunk = L; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -203,11 +225,12 @@ extern "C" int hs_autotune(const double* c, double omega, int n, int dim, int pm
   if (st != HS_OK) return st;
   if (*best_chunk == 0) return HS_EUNSUPPORTED;
   if (best_ms) *best_ms = best;
+  if (best_sep) *best_sep = bsep;
   if (opt_in && opt_in->tune_cache) {
     FILE* f = std::fopen(opt_in->tune_cache, "a");
     if (!f) return HS_EINVAL;
-    std::fprintf(f, "2d n=%d bp=%d b=%d d=%d prec=%d nrhs=%d chunk=%d ms=%.4f\n", n, pml_width, moving_pml_width,
-                 opt.layers_per_step, opt.factor_prec, nrhs, *best_chunk, best);
+    std::fprintf(f, "2d n=%d bp=%d b=%d d=%d prec=%d nrhs=%d chunk=%d sep=%d ms=%.4f\n", n, pml_width,
+                 moving_pml_width, opt.layers_per_step, opt.factor_prec, nrhs, *best_chunk, bsep, best);
     std::fclose(f);
   }
   return HS_OK;

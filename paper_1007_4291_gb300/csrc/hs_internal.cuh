@@ -161,7 +161,9 @@ int sweep_internal(Plan& p, int nrhs, cudaStream_t s, bool graph = false);
 int sweep_launch(Plan& p, int nrhs, cudaStream_t s);
 void release_sweep_graphs(Plan& p);
 // chunk length stored by hs_autotune in `path` for this key (0 if none)
-int tuned_chunk(const char* path, int n, int bp, int b, int dL, int prec, int nrhs);
+// chunk length (and separator grouping in *sep, 0 if not recorded) stored by
+// hs_autotune for this key, or 0
+int tuned_chunk(const char* path, int n, int bp, int b, int dL, int prec, int nrhs, int* sep);
 // drop cached multi-plan graphs that contain plan `uid` (hs_batch.cu)
 void forget_batch_graphs(long long uid);
 // largest separator count per x1 partition the separator solve supports for

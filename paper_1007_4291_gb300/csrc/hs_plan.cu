@@ -123,6 +123,7 @@ extern "C" int hs_default_options(hs_options* opt) {
   opt->krylov_basis = 1;
   opt->inner_tol = 1e-4;
   opt->tune_cache = nullptr;
+  opt->sep_rhs_per_cta = 0;
   return HS_OK;
 }
 
@@ -283,6 +284,8 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
   if (opt.factor_prec != HS_C64 && opt.factor_prec != HS_C128) return HS_EINVAL;
   if ((opt.krylov_basis != 0 && opt.krylov_basis != 1) || !(opt.inner_tol > 0.0 && opt.inner_tol < 1.0))
     return HS_EINVAL;
+  if (opt.sep_rhs_per_cta != 0 && opt.sep_rhs_per_cta != 1 && opt.sep_rhs_per_cta != 2 && opt.sep_rhs_per_cta != 4)
+    return HS_EINVAL;
   for (long long k = 0; k < (long long)n * n; ++k)
     if (!(c[k] > 0.0) || !std::isfinite(c[k])) return HS_EINVAL;
 
@@ -302,8 +305,12 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
   // right-hand sides of all separators of a chain in shared memory, which
   // bounds the separator count.
   int chunk = opt.chunk;
-  if (chunk == 0) chunk = tuned_chunk(opt.tune_cache, n, pml_width, moving_pml_width, opt.layers_per_step,
-                                      opt.factor_prec, opt.max_nrhs);
+  if (chunk == 0) {
+    int sep = 0;
+    chunk = tuned_chunk(opt.tune_cache, n, pml_width, moving_pml_width, opt.layers_per_step, opt.factor_prec,
+                        opt.max_nrhs, &sep);
+    if (chunk && opt.sep_rhs_per_cta == 0) p->opt.sep_rhs_per_cta = sep;
+  }
   p->opt.tune_cache = nullptr;  // the string belongs to the caller
   if (!chunk) {
     int dev = 0, sms = 0;

@@ -913,7 +913,7 @@ int run_stage_w(const Plan& p, SweepArgs a, cudaStream_t s) {
   const size_t sm1 = tile_smem<R, W>(dmax, false);
   const size_t sm3 = tile_smem<R, W>(dmax, true);
   set_attrs_w<R, W>();
-  const int wpc = phase2_wpc(a.R, a.nfront);
+  const int wpc = p.opt.sep_rhs_per_cta > 0 ? p.opt.sep_rhs_per_cta : phase2_wpc(a.R, a.nfront);
   if (sm1 > 220 * 1024 || sm3 > 220 * 1024 || phase2_smem<R, W>(a.P - 1, wpc) > 220 * 1024) return HS_EUNSUPPORTED;
   dim3 g13(a.P, (a.R + TL::RG - 1) / TL::RG, a.nfront);
   note_launch();

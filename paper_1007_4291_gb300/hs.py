@@ -32,7 +32,7 @@ class HsOptions(ctypes.Structure):
                 ("factor_prec", ctypes.c_int), ("chunk", ctypes.c_int), ("max_nrhs", ctypes.c_int),
                 ("restart", ctypes.c_int), ("reorth", ctypes.c_int), ("spin_budget", ctypes.c_longlong),
                 ("graphs", ctypes.c_int), ("krylov_basis", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("frontal_gemm", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
+                ("frontal_gemm", ctypes.c_int), ("tune_cache", ctypes.c_char_p), ("sep_rhs_per_cta", ctypes.c_int)]
 
 
 class HsSolveInfo(ctypes.Structure):
@@ -71,7 +71,7 @@ def load(path=None):
     lib.hs_apply_batched.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(i), i, vp]
     lib.hs_autotune.argtypes = [vp, d, i, i, i, i, ctypes.POINTER(HsOptions), i, vp, ctypes.POINTER(i),
-                                ctypes.POINTER(d)]
+                                ctypes.POINTER(d), ctypes.POINTER(i)]
     lib.hs_matvec.argtypes = [vp, vp, vp, i, i, vp]
     lib.hs_apply_noalloc.argtypes = [vp, vp, vp, i, i, vp]
     lib.hs_apply_noalloc.restype = i
@@ -198,15 +198,16 @@ def hs_apply_batched(plans, rs, zs, nrhs, dtype, stream=None):
 
 
 def hs_autotune(c, omega, n, dim, pml_width, moving_pml_width, nrhs, opt=None, stream=None):
-    """Time the candidate chunk lengths; returns (best chunk, ms per application)."""
+    """Time the candidate chunk lengths and separator groupings; returns
+    (best chunk, ms per application, RHS per separator-solve CTA)."""
     lib = load()
     c = np.ascontiguousarray(c, dtype=np.float64)
     o = opt if opt is not None else hs_default_options()
-    best, ms = ctypes.c_int(), ctypes.c_double()
+    best, ms, sep = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
     _check(lib.hs_autotune(c.ctypes.data, float(omega), int(n), int(dim), int(pml_width), int(moving_pml_width),
-                           ctypes.byref(o), int(nrhs), _stream(stream), ctypes.byref(best), ctypes.byref(ms)),
-           "hs_autotune")
-    return best.value, ms.value
+                           ctypes.byref(o), int(nrhs), _stream(stream), ctypes.byref(best), ctypes.byref(ms),
+                           ctypes.byref(sep)), "hs_autotune")
+    return best.value, ms.value, sep.value
 
 
 def hs_cnn_create(params):

@@ -102,6 +102,23 @@ def test_batched_setup_with_options_per_problem():
             hs.hs_destroy(p)
 
 
+@pytest.mark.parametrize("sep", [1, 2, 4])
+def test_separator_grouping_option_gives_the_same_result(sep):
+    """Any fixed number of RHS per separator-solve CTA (the autotuner's
+    second knob) computes the same arithmetic per RHS: bit-identical to the
+    automatic choice."""
+    n = 63
+    c = I.random_velocity(n, 14)
+    pa = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(max_nrhs=7, graphs=0))
+    pf = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(max_nrhs=7, sep_rhs_per_cta=sep))
+    try:
+        r = torch.from_numpy(I.random_rhs(n, 7, 15)).to("cuda").to(torch.complex64)   # 7: a ragged last group
+        assert torch.equal(apply_direct(pa, r, 7), apply_direct(pf, r, 7))
+    finally:
+        hs.hs_destroy(pa)
+        hs.hs_destroy(pf)
+
+
 @pytest.mark.parametrize("nrhs", [100, 160])     # two and four RHS per separator-solve CTA
 def test_many_rhs_match_the_same_rhs_in_slices(nrhs):
     """The separator solve groups more RHS per CTA when the RHS of both
@@ -174,13 +191,13 @@ def test_autotune_writes_cache_that_setup_reads(tmp_path):
     c = I.random_velocity(n, 5)
     cache = str(tmp_path / "tune.txt")
     o = opts(max_nrhs=2, chunk=0, tune_cache=cache)
-    best, ms = hs.hs_autotune(c.ravel(), omega_of(n), n, 2, BP, BP, 2, opt=o)
-    assert best >= 2 and ms > 0
+    best, ms, sep = hs.hs_autotune(c.ravel(), omega_of(n), n, 2, BP, BP, 2, opt=o)
+    assert best >= 2 and ms > 0 and sep in (1, 2, 4)
     line = open(cache).read().strip().splitlines()[-1]
-    assert ("n=%d" % n) in line and ("chunk=%d" % best) in line
+    assert ("n=%d" % n) in line and ("chunk=%d" % best) in line and ("sep=%d" % sep) in line
     # a setup with chunk = 0 and the cache gives the same operator as chunk = best
     pt = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(max_nrhs=2, chunk=0, tune_cache=cache))
-    pe = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(max_nrhs=2, chunk=best))
+    pe = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(max_nrhs=2, chunk=best, sep_rhs_per_cta=sep))
     try:
         r = torch.from_numpy(I.random_rhs(n, 2, 4)).to("cuda").to(torch.complex64)
         assert torch.equal(apply_direct(pt, r, 2), apply_direct(pe, r, 2))
