@@ -82,7 +82,7 @@ typedef struct {
                             The string must outlive the hs_setup call.                        default NULL */
   int sep_rhs_per_cta;   /* RHS per CTA of the separator solve (phase 2 of every sweep stage):
                             0 picks one while the RHS of both fronts fit on the SMs one CTA each,
-                            else two or four; 1, 2 or 4 fix it.                               default 0 */
+                            else two or four; 1, 2 or 4 fix it (complex128 factors: at most two). default 0 */
 } hs_options;
 
 typedef struct hs_plan hs_plan;

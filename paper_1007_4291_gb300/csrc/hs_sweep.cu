@@ -418,33 +418,46 @@ __global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase1_kernel(SweepA
 
 // ---------------------------------------------------------------- phase 2
 // Twisted block LU solve of the separator system (see the setup): for each
-// RHS a top warp and a bottom warp run the two half chains at once,
+// RHS the top half and the bottom half run the two half chains at once,
 //   top     psi_k  = rho_k - F_k psi_{k-1}            k = 0 .. m-1
 //   bottom  psi'_k = rho_k - F'_k psi'_{k+1}          k = K-1 .. m+1
 //   twist   x_m = Gamma_m (rho_m - F_m psi_{m-1} - F'_m psi'_{m+1})
 //   top     x_k = Gamma_k psi_k - F_{k+1}^t x_{k+1}    k = m-1 .. 0
 //   bottom  x_k = Gamma'_k psi'_k - F'_{k-1}^t x_{k-1} k = m+1 .. K-1
-// (lane p = row p).  rho_k = -(rc_k + lc_{k+1}) is gathered into shared
-// memory first; the chain variables are exchanged there (broadcast loads).
-// The two warps of a RHS meet twice on a named barrier (psi'_{m+1}, then
-// x_m); each half has its own producer warp streaming the separator factors
-// through an S2-deep TMA ring in the order its chain uses them.
+// (lane p = row p).  Each half is two warps that split the W columns of
+// every block product: each forms the partial sums of its columns, they
+// exchange them through shared memory on a named barrier (which also
+// carries their agreement on the bounded waits), and both finish the step,
+// so each keeps the chain variable it needs in its own registers and
+// shared-memory copy.  rho_k = -(rc_k + lc_{k+1}) is gathered into shared
+// memory first.  The four warps of a RHS meet twice on a named barrier
+// (psi'_{m+1}, then x_m); each half has its own producer warp streaming the
+// separator factors through an S2-deep TMA ring in the order its chain uses
+// them.
 // RHS per CTA (wpc, from the block size): one while the RHS of both fronts
-// fit on the SMs one CTA each (the chain warps then have a scheduler each,
-// on SMs the chunk phases leave idle), else two or four so that the
-// separator solve stays within one wave.
+// fit on the SMs one CTA each (the chain warps then run on SMs the chunk
+// phases leave idle), else two or four so that the separator solve stays
+// within one wave.
 constexpr int WPC_MAX = 4;
+// Column parts per half: two for complex64; complex128 keeps one warp per
+// half (its products are bound by the FP64 pipe, and the exchange only adds
+// latency there), with at most two RHS per CTA so that the threads keep the
+// registers of the double-precision products.
+template <typename R> constexpr int npart() { return sizeof(R) == 4 ? 2 : 1; }
+template <typename R> constexpr int wpc_max() { return sizeof(R) == 4 ? WPC_MAX : 2; }
 // TMA ring depth: 4 stages per half, 2 when the separator factors are large
 template <typename R, int W> struct Ring2 {
   static constexpr int S = (8LL * 3 * W * (W + 2) * 2 * (long long)sizeof(R) <= 128 * 1024) ? 4 : 2;
 };
 
+// per RHS: rho/psi [K] + x_m + two exchange vectors (one per half) and the
+// partial sums [step parity][half][part]
 template <typename R, int W>
-size_t phase2_smem(int nsep, int wpc = WPC_MAX) {
+size_t phase2_smem(int nsep, int wpc) {
   return 256 + (size_t)2 * Ring2<R, W>::S * round128((size_t)red_elems(W) * sizeof(cplx<R>)) +
-         (size_t)wpc * (nsep + 3) * W * sizeof(cplx<R>);
+         (size_t)wpc * ((nsep + 3) * W + 8 * W) * sizeof(cplx<R>);
 }
-int phase2_wpc(int R, int nfront) {
+int phase2_wpc(int R, int nfront, int maxw) {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -452,29 +465,32 @@ int phase2_wpc(int R, int nfront) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
   int wpc = 1;
-  while (wpc < WPC_MAX && (long long)((R + wpc - 1) / wpc) * nfront > sms) wpc *= 2;
+  while (wpc < maxw && (long long)((R + wpc - 1) / wpc) * nfront > sms) wpc *= 2;
   return wpc;
 }
 
-// Named barrier of the two warps of one RHS, returning the AND of `v`.
-__device__ __forceinline__ bool pair_barrier_and(int id, bool v) {
+// Named barrier of `nthreads` threads, returning the AND of `v` over them.
+__device__ __forceinline__ bool named_barrier_and(int id, int nthreads, bool v) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.and.pred q, %2, 64, p;\n\t"
+      "bar.red.and.pred q, %2, %3, p;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}"
       : "=r"(r)
-      : "r"((uint32_t)v), "r"(id)
+      : "r"((uint32_t)v), "r"(id), "r"(nthreads)
       : "memory");
   return r != 0;
 }
 
 template <typename R, int W>
-__global__ void __launch_bounds__(2 * WPC_MAX * 32 + 64) phase2_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(2 * npart<R>() * wpc_max<R>() * 32 + 64) phase2_kernel(SweepArgs a) {
   using C = cplx<R>;
   constexpr int LDP = W + 2;
   constexpr int S2 = Ring2<R, W>::S;
+  constexpr int NP = npart<R>();     // column parts per half
+  constexpr int P2W = 2 * NP;        // consumer warps per RHS
+  constexpr int WH = W / NP;         // columns per part (even for every supported W)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);     // [2][S2]
   uint64_t* empty = full + 2 * S2;                            // [2][S2]
@@ -488,7 +504,7 @@ __global__ void __launch_bounds__(2 * WPC_MAX * 32 + 64) phase2_kernel(SweepArgs
   C* rz = reinterpret_cast<C*>(smem_raw + 256 + (size_t)2 * S2 * sstride);
   const C* red = reinterpret_cast<const C*>(a.red) + d.red_off;
   const int tid = threadIdx.x;
-  const int wpc = ((int)blockDim.x - 64) / 64;   // RHS per CTA (two consumer warps each)
+  const int wpc = ((int)blockDim.x - 64) / (P2W * 32);   // RHS per CTA
   auto stage = [&](int h, int u) { return reinterpret_cast<C*>(smem_raw + 256 + (size_t)(h * S2 + u % S2) * sstride); };
   // separator of use u of half h
   auto slot_of = [&](int h, int u) {
@@ -499,13 +515,13 @@ __global__ void __launch_bounds__(2 * WPC_MAX * 32 + 64) phase2_kernel(SweepArgs
   if (tid == 0) {
     for (int u = 0; u < 2 * S2; ++u) {
       mbar_init(&full[u], 1);
-      mbar_init(&empty[u], wpc);
+      mbar_init(&empty[u], NP * wpc);    // every column part of every RHS releases each use
     }
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid >= 2 * wpc * 32) {
-    const int h = (tid - 2 * wpc * 32) >> 5;
+  if (tid >= P2W * wpc * 32) {
+    const int h = (tid - P2W * wpc * 32) >> 5;
     if ((tid & 31) == 0 && nuse[h] > 0)
       ring_producer(full + h * S2, empty + h * S2, S2, nuse[h], a.spin, a.status, front, [&](int t) {
         mbar_arrive_expect_tx(&full[h * S2 + t % S2], rbytes);
@@ -514,21 +530,29 @@ __global__ void __launch_bounds__(2 * WPC_MAX * 32 + 64) phase2_kernel(SweepArgs
     return;
   }
   const int lane = tid & 31, wq = tid >> 5;
-  const int rhs = wq % wpc, half = wq / wpc;
+  const int rhs = wq % wpc, role = wq / wpc, half = role / NP, part = role % NP;
+  const int q0 = part * WH;          // first column of this warp's part
   const int r = blockIdx.y * wpc + rhs;
   const bool valid = r < a.R;
   const int rr = valid ? r : (a.R - 1);
   const int pl = lane < W ? lane : 0;
+  const int pair_id = 1 + rhs, half_id = 1 + WPC_MAX + 2 * rhs + half;
   const C* rcb = reinterpret_cast<const C*>(a.rc);
   const C* lcb = reinterpret_cast<const C*>(a.lc);
   C* xsb = reinterpret_cast<C*>(a.xs);
   const long long fb = (long long)front * a.P;
-  C* myrz = rz + (size_t)rhs * (K + 3) * W;    // [0..K-1] rho/psi, [K] x_m, [K+1+half] own exchange
+  // [0..K-1] rho/psi, [K] x_m, [K+1+half] exchange of the half, then the
+  // partial sums [parity][half][part][W]
+  C* myrz = rz + (size_t)rhs * ((K + 3) * W + 8 * W);
   C* xm = myrz + (size_t)K * W;
   C* xch = myrz + (size_t)(K + 1 + half) * W;
+  C* pbuf = myrz + (size_t)(K + 3) * W;
+  auto my_part = [&](int par) { return pbuf + ((par * 2 + half) * 2 + part) * W; };
+  auto other_part = [&](int par) { return pbuf + ((par * 2 + half) * 2 + (1 - part)) * W; };
   uint64_t* fl = full + half * S2;
   uint64_t* em = empty + half * S2;
-  // rho_k of this half's separators (top: 0..m, bottom: m+1..K-1)
+  // rho_k of this half's separators (top: 0..m, bottom: m+1..K-1); both
+  // parts write the same values
   const int k_lo = half == 0 ? 0 : m + 1, k_hi = half == 0 ? m + 1 : K;
   for (int k0 = k_lo; k0 < k_hi; k0 += 16) {
     C v1[16], v2[16];
@@ -543,151 +567,156 @@ __global__ void __launch_bounds__(2 * WPC_MAX * 32 + 64) phase2_kernel(SweepArgs
       if (k0 + q < k_hi && lane < W) myrz[(k0 + q) * W + lane] = C{-(v1[q].re + v2[q].re), -(v1[q].im + v2[q].im)};
   }
   __syncwarp();
-  bool ok = true;
-  int t = 0;
-  // y = v - Mrow * prev with Mrow the row pl of a W x W block (row stride
-  // LDP).  Rows start on 16-byte boundaries (W even), so both operands move
-  // two complex values per shared-memory access; the row reads of one
-  // quarter warp fall in distinct bank groups (LDP/2 is odd).
-  auto row_apply = [&](C v, const C* Mrow, const C* prev) {
-    C s1{0, 0}, s2{0, 0}, s3{0, 0};
+  // partial sum over this part's columns of row pl of a W x W block (row
+  // stride LDP) times a W-vector in shared memory.  Rows and vectors start on
+  // 16-byte boundaries (W and WH even), so both move two complex values per
+  // access; the row reads of one quarter warp fall in distinct bank groups.
+  auto part_dot = [&](const C* Mrow, const C* vec) {
+    C s[4] = {C{0, 0}, C{0, 0}, C{0, 0}, C{0, 0}};
 #pragma unroll
-    for (int q = 0; q < W; q += 4) {
-      C m0, m1, m2, m3, p0, p1, p2, p3;
-      ld2(Mrow + q, m0, m1);
-      ld2(Mrow + q + 2, m2, m3);
-      ld2(prev + q, p0, p1);
-      ld2(prev + q + 2, p2, p3);
-      cfms(v, m0, p0);
-      cfms(s1, m1, p1);
-      cfms(s2, m2, p2);
-      cfms(s3, m3, p3);
+    for (int q = 0; q < WH; q += 2) {
+      C m0, m1, p0, p1;
+      ld2(Mrow + q0 + q, m0, m1);
+      ld2(vec + q0 + q, p0, p1);
+      cfma(s[q & 3], m0, p0);
+      cfma(s[(q & 3) + 1], m1, p1);
     }
-    return cadd(cadd(v, s1), cadd(s2, s3));
+    return cadd(cadd(s[0], s[1]), cadd(s[2], s[3]));
   };
-  // Gamma * ps for the symmetric Gamma (row pl read in place of column pl)
-  auto gamma_apply = [&](const C* Gm, const C* ps, C& s0, C& s1, C& s2, C& s3) {
-    const C* Grow = Gm + pl * LDP;
+  // partial of F^t x over this part's rows of F (F's column pl held in fc)
+  auto fcol_dot = [&](const C (&fc)[WH], const C* xv) {
+    C s[4] = {C{0, 0}, C{0, 0}, C{0, 0}, C{0, 0}};
 #pragma unroll
-    for (int q = 0; q < W; q += 4) {
-      C g0, g1, g2, g3, p0, p1, p2, p3;
-      ld2(Grow + q, g0, g1);
-      ld2(Grow + q + 2, g2, g3);
-      ld2(ps + q, p0, p1);
-      ld2(ps + q + 2, p2, p3);
-      cfma(s0, g0, p0);
-      cfma(s1, g1, p1);
-      cfma(s2, g2, p2);
-      cfma(s3, g3, p3);
+    for (int q = 0; q < WH; q += 2) {
+      C x0, x1;
+      ld2(xv + q0 + q, x0, x1);
+      cfma(s[q & 3], fc[q], x0);
+      cfma(s[(q & 3) + 1], fc[q + 1], x1);
     }
+    return cadd(cadd(s[0], s[1]), cadd(s[2], s[3]));
   };
-  // s -= F^t x with F's column pl held in fcol
-  auto fcol_apply = [&](const C (&fc)[W], const C* xv, C& s0, C& s1, C& s2, C& s3) {
+  auto load_fcol = [&](C (&fc)[WH], const C* Fblk) {   // column pl of F, this part's rows
 #pragma unroll
-    for (int q = 0; q < W; q += 4) {
-      C x0, x1, x2, x3;
-      ld2(xv + q, x0, x1);
-      ld2(xv + q + 2, x2, x3);
-      cfms(s0, fc[q], x0);
-      cfms(s1, fc[q + 1], x1);
-      cfms(s2, fc[q + 2], x2);
-      cfms(s3, fc[q + 3], x3);
+    for (int q = 0; q < WH; ++q) fc[q] = Fblk[(q0 + q) * LDP + pl];
+  };
+  // both parts publish their partial sums and meet; the result is the AND of
+  // `landed` over the two warps, and on success `total` is part 0's partial
+  // plus part 1's in that order (the same bits in both warps)
+  int sc = 0;
+  auto exchange = [&](C own, bool landed, C& total) {
+    if constexpr (NP == 1) {        // one warp per half: its own agreement
+      total = own;
+      return landed;
     }
+    const int par = sc++ & 1;
+    if (lane < W) my_part(par)[lane] = own;
+    const bool both = named_barrier_and(half_id, 64, landed);
+    if (both) {
+      const C oth = other_part(par)[pl];
+      total = part == 0 ? cadd(own, oth) : cadd(oth, own);
+    }
+    return both;
   };
-  auto wait_use = [&](int u) {
-    if (ok) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&fl[u % S2], (u / S2) & 1, a.spin));
-    return ok;
-  };
+  auto waitp = [&](int u) { return __all_sync(0xffffffffu, mbar_wait_bounded(&fl[u % S2], (u / S2) & 1, a.spin)); };
   auto release = [&](int u) {
     __syncwarp();
     if (lane == 0) mbar_arrive(&em[u % S2]);
   };
-  // ---- forward half chains
+  bool ok = true;
+  int t = 0;
+  // ---- forward half chains: every step ends with the parts' exchange, so a
+  // step with no product (the first) still carries the wait agreement
   if (half == 0) {
     for (int k = 0; k < m; ++k, ++t) {
-      if (!wait_use(t)) break;
-      if (k > 0) {
-        const C psi = row_apply(myrz[k * W + pl], stage(0, t) + W * LDP + pl * LDP, myrz + (k - 1) * W);
-        __syncwarp();
-        if (lane < W) myrz[k * W + lane] = psi;
-      }
+      const bool landed = waitp(t);
+      const C v = myrz[k * W + pl];            // rho_k, read before the exchange
+      C own{0, 0}, tot{0, 0};
+      if (landed && k > 0) own = part_dot(stage(0, t) + W * LDP + pl * LDP, myrz + (k - 1) * W);
+      ok = exchange(own, landed, tot);
+      if (!ok) break;
+      if (k > 0 && lane < W) myrz[k * W + lane] = csub(v, tot);
       release(t);
     }
   } else {
     for (int u = 0; u < nb; ++u, ++t) {
       const int k = K - 1 - u;
-      if (!wait_use(t)) break;
-      if (k < K - 1) {
-        const C psi = row_apply(myrz[k * W + pl], stage(1, t) + W * LDP + pl * LDP, myrz + (k + 1) * W);
-        __syncwarp();
-        if (lane < W) myrz[k * W + lane] = psi;
-      }
+      const bool landed = waitp(t);
+      const C v = myrz[k * W + pl];
+      C own{0, 0}, tot{0, 0};
+      if (landed && k < K - 1) own = part_dot(stage(1, t) + W * LDP + pl * LDP, myrz + (k + 1) * W);
+      ok = exchange(own, landed, tot);
+      if (!ok) break;
+      if (k < K - 1 && lane < W) myrz[k * W + lane] = csub(v, tot);
       release(t);
     }
   }
-  ok = pair_barrier_and(1 + rhs, ok);
-  // ---- twist (top warp)
-  C fcol[W];
+  ok = named_barrier_and(pair_id, P2W * 32, ok);
+  // ---- twist (top half)
+  C fcol[WH];
   if (half == 0 && ok) {
-    if (wait_use(t)) {
-      const C* Gm = stage(0, t);
-      C v = myrz[m * W + pl];
-      if (m >= 1) v = row_apply(v, Gm + W * LDP + pl * LDP, myrz + (m - 1) * W);
-      if (m < K - 1) v = row_apply(v, Gm + 2 * W * LDP + pl * LDP, myrz + (m + 1) * W);
+    const bool landed = waitp(t);
+    const C* Gm = stage(0, t);
+    const C v = myrz[m * W + pl];
+    C own{0, 0}, tot{0, 0}, x{0, 0};
+    if (landed) {
+      if (m >= 1) own = part_dot(Gm + W * LDP + pl * LDP, myrz + (m - 1) * W);
+      if (m < K - 1) own = cadd(own, part_dot(Gm + 2 * W * LDP + pl * LDP, myrz + (m + 1) * W));
+    }
+    ok = exchange(own, landed, tot);
+    own = C{0, 0};
+    if (ok) {
+      if (lane < W) xch[lane] = csub(v, tot);  // both parts write the same vector
       __syncwarp();
-      if (lane < W) xch[lane] = v;
-      __syncwarp();
-      C s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
-      gamma_apply(Gm, xch, s0, s1, s2, s3);
-      const C x = cadd(cadd(s0, s1), cadd(s2, s3));
-#pragma unroll
-      for (int q = 0; q < W; ++q) fcol[q] = Gm[W * LDP + q * LDP + pl];   // F_m column p
+      own = part_dot(Gm + pl * LDP, xch);     // Gamma_m is symmetric: row pl for column pl
+    }
+    ok = exchange(own, ok, x);
+    if (ok) {
+      load_fcol(fcol, Gm + W * LDP);           // F_m
       __syncwarp();
       if (lane < W) { xm[lane] = x; xch[lane] = x; }
-      if (valid && lane < W) xsb[((fb + m) * a.R + r) * W + lane] = x;
+      if (valid && part == 0 && lane < W) xsb[((fb + m) * a.R + r) * W + lane] = x;
       release(t);
       ++t;
     }
   }
-  ok = pair_barrier_and(1 + rhs, ok);
+  ok = named_barrier_and(pair_id, P2W * 32, ok);
   // ---- backward half chains
   if (half == 0 && ok) {
     for (int k = m - 1; k >= 0; --k, ++t) {
-      if (!wait_use(t)) break;
+      const bool landed = waitp(t);
       const C* Gm = stage(0, t);
-      C s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
-      gamma_apply(Gm, myrz + k * W, s0, s1, s2, s3);
-      fcol_apply(fcol, xch, s0, s1, s2, s3);   // - F_{k+1}^t x_{k+1}
-      const C x = cadd(cadd(s0, s1), cadd(s2, s3));
-#pragma unroll
-      for (int q = 0; q < W; ++q) fcol[q] = Gm[W * LDP + q * LDP + pl];
+      C own{0, 0}, x{0, 0};
+      if (landed) own = csub(part_dot(Gm + pl * LDP, myrz + k * W), fcol_dot(fcol, xch));   // Gamma_k psi_k - F_{k+1}^t x_{k+1}
+      ok = exchange(own, landed, x);
+      if (!ok) break;
+      load_fcol(fcol, Gm + W * LDP);           // F_k for the next step
       __syncwarp();
       if (lane < W) xch[lane] = x;
-      if (valid && lane < W) xsb[((fb + k) * a.R + r) * W + lane] = x;
+      if (valid && part == 0 && lane < W) xsb[((fb + k) * a.R + r) * W + lane] = x;
       release(t);
     }
   } else if (half == 1 && ok && nb > 0) {
     // F'_m column from the twist slot, then k = m+1 .. K-1
-    if (wait_use(t)) {
-      const C* Gm = stage(1, t);
-#pragma unroll
-      for (int q = 0; q < W; ++q) fcol[q] = Gm[2 * W * LDP + q * LDP + pl];
+    const bool landed = waitp(t);
+    if (landed) load_fcol(fcol, stage(1, t) + 2 * W * LDP);
+    C dummy{0, 0};
+    ok = exchange(C{0, 0}, landed, dummy);
+    if (ok) {
       __syncwarp();
       if (lane < W) xch[lane] = xm[lane];
       release(t);
       ++t;
       for (int k = m + 1; k < K; ++k, ++t) {
-        if (!wait_use(t)) break;
+        const bool landed2 = waitp(t);
         const C* Gk = stage(1, t);
-        C s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
-        gamma_apply(Gk, myrz + k * W, s0, s1, s2, s3);
-        fcol_apply(fcol, xch, s0, s1, s2, s3);   // - F'_{k-1}^t x_{k-1}
-        const C x = cadd(cadd(s0, s1), cadd(s2, s3));
-#pragma unroll
-        for (int q = 0; q < W; ++q) fcol[q] = Gk[W * LDP + q * LDP + pl];
+        C own{0, 0}, x{0, 0};
+        if (landed2) own = csub(part_dot(Gk + pl * LDP, myrz + k * W), fcol_dot(fcol, xch));   // - F'_{k-1}^t x_{k-1}
+        ok = exchange(own, landed2, x);
+        if (!ok) break;
+        load_fcol(fcol, Gk + W * LDP);
         __syncwarp();
         if (lane < W) xch[lane] = x;
-        if (valid && lane < W) xsb[((fb + k) * a.R + r) * W + lane] = x;
+        if (valid && part == 0 && lane < W) xsb[((fb + k) * a.R + r) * W + lane] = x;
         release(t);
       }
     }
@@ -913,7 +942,8 @@ int run_stage_w(const Plan& p, SweepArgs a, cudaStream_t s) {
   const size_t sm1 = tile_smem<R, W>(dmax, false);
   const size_t sm3 = tile_smem<R, W>(dmax, true);
   set_attrs_w<R, W>();
-  const int wpc = p.opt.sep_rhs_per_cta > 0 ? p.opt.sep_rhs_per_cta : phase2_wpc(a.R, a.nfront);
+  const int wpc = p.opt.sep_rhs_per_cta > 0 ? std::min(p.opt.sep_rhs_per_cta, wpc_max<R>())
+                                            : phase2_wpc(a.R, a.nfront, wpc_max<R>());
   if (sm1 > 220 * 1024 || sm3 > 220 * 1024 || phase2_smem<R, W>(a.P - 1, wpc) > 220 * 1024) return HS_EUNSUPPORTED;
   dim3 g13(a.P, (a.R + TL::RG - 1) / TL::RG, a.nfront);
   note_launch();
@@ -921,7 +951,7 @@ int run_stage_w(const Plan& p, SweepArgs a, cudaStream_t s) {
   if (a.P > 1) {
     dim3 g2(1, (a.R + wpc - 1) / wpc, a.nfront);
     note_launch();
-    phase2_kernel<R, W><<<g2, 2 * wpc * 32 + 64, phase2_smem<R, W>(a.P - 1, wpc), s>>>(a);
+    phase2_kernel<R, W><<<g2, 2 * npart<R>() * wpc * 32 + 64, phase2_smem<R, W>(a.P - 1, wpc), s>>>(a);
   }
   note_launch();
   phase3_kernel<R, W><<<g13, TL::NCONS + 32, sm3, s>>>(a);
@@ -1024,7 +1054,7 @@ namespace {
 template <typename R, int W>
 int max_sep_w() {
   int k = 1;
-  while (k < 4096 && phase2_smem<R, W>(k + 1) <= 220 * 1024) ++k;
+  while (k < 4096 && phase2_smem<R, W>(k + 1, wpc_max<R>()) <= 220 * 1024) ++k;   // the largest CTA
   return k;
 }
 template <typename R>
