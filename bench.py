@@ -180,7 +180,7 @@ def oracle_sample(wl, nrhs, iters, budget_s=20.0):
     t0 = time.perf_counter()
     for blk in lower[1:]:
         ta = time.perf_counter()
-        fb = S.factor_block(blk, wl["c"], wl["omega"], bp, b, wl["C"], wl["alpha"], Cm=2.0 * wl["C"])
+        fb = S.factor_block(blk, wl["c"], wl["omega"], bp, b, wl["C"], wl["alpha"])
         tb = time.perf_counter()
         fb.t_tilde(r[:, blk.lo - 1:blk.hi, :])
         tc = time.perf_counter()

@@ -50,8 +50,11 @@ enum { HS_C64 = 64, HS_C128 = 128 };
 typedef struct {
   double alpha;          /* alpha of Eq. helmalpha: the subproblems use (omega + i alpha)^2 / c^2.   default 2 */
   double pml_C;          /* C of Eq. sigma: strength of the boundary PML (part of the operator A).    default 20 */
-  double moving_pml_C;   /* strength of the moving PMLs of the subproblems (Eq. helma): a parameter
-                            of the preconditioner only.                                          default 40 */
+  double moving_pml_C;   /* strength of the moving PMLs of the subproblems (Eq. helma).  0: the
+                            boundary PML's pml_C, the single constant C that Eq. helma reuses
+                            through sigma_2 (the paper's preconditioner); > 0: a separate
+                            strength, a tuning of the preconditioner only (the operator A and
+                            its solution do not change).                                      default 0 */
   int layers_per_step;   /* d of Sec. 2.3 (rows eliminated per sweep step).                           default 12 */
   int factor_prec;       /* HS_C64: complex float factors and sweep; HS_C128: complex double.          default HS_C64 */
   int chunk;             /* x1 columns per partition chunk (>= 2).  0: ceil(n / (SMs/2)), one chunk
@@ -172,17 +175,24 @@ int hs_apply(hs_plan* plan, const void* r, void* z, int nrhs, int dtype, void* s
  *
  * It allocates nothing: all temporaries (working vector, chunk store,
  * separator buffers) live in one file-scope device array of 32 MiB that every
- * device loading the library holds until the process exits; the plan's own
- * workspace is not used.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Calls share the array and it keeps
- * the last call's contents (nothing in it needs to start at zero), so calls
- * that overlap on the GPU race: serialise them.  Returns HS_EINVAL when the
- * problem does not fit: n*n*nrhs + 2*n*nrhs*Wmax + 8*P*nrhs*Wmax elements of
- * the factor precision (Wmax <= 32 the padded window height, P the number of
- * x1 chunks), each rounded up to 256 bytes, must not exceed 32 MiB (for
- * example n = 511 with up to 13 right-hand sides in complex64).
- * Arguments as hs_apply.
+ * device loading the library holds until the process exits.  The plan is
+ * only read (its factors and tables); its own workspace is not touched, so
+ * hs_apply, hs_solve or hs_matvec on the same plan may run at the same time
+ * as this call.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Calls of this entry point share the array
+ * and it keeps the last call's contents (nothing in it needs to start at
+ * zero), so two hs_apply_noalloc calls that overlap on the GPU race:
+ * serialise them.  Result: bit for bit that of hs_apply (same kernels, same
+ * launch shapes).
+ *
+ * Arguments as hs_apply (2D plans; HS_EUNSUPPORTED for 3D).  Returns HS_EINVAL
+ * when nrhs is outside 1..max_nrhs, when the current device is not the one
+ * the plan was set up on, or when the problem does not fit:
+ * n*n*nrhs + 2*n*nrhs*Wmax + 8*P*nrhs*Wmax elements of the factor precision
+ * (Wmax <= 32 the padded window height, P the number of x1 chunks), each
+ * rounded up to 256 bytes, must not exceed 32 MiB (for example n = 511 with
+ * up to 13 right-hand sides in complex64).
  */
 int hs_apply_noalloc(hs_plan* plan, const void* r, void* z, int nrhs, int dtype, void* stream);
 

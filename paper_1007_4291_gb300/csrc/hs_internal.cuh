@@ -74,6 +74,7 @@ struct Plan {
   int n = 0, dim = 2, bp = 0, b = 0, dL = 1;
   double omega = 0, alpha = 0, C = 0, Cm = 0, h = 0;   // C boundary PML, Cm moving PMLs
   int prec = HS_C64;  // factor precision
+  int device = 0;     // CUDA device current at setup (owns every device buffer of the plan)
   int L = 32, P = 1;  // x1 chunk length and chunk count
   int max_nrhs = 64;
   hs_options opt{};
@@ -159,6 +160,14 @@ int launch_setup(const std::vector<Plan*>& ps, cudaStream_t s);
 int sweep_internal(Plan& p, int nrhs, cudaStream_t s, bool graph = false);
 // direct launches of the stage chain (used inside captures)
 int sweep_launch(Plan& p, int nrhs, cudaStream_t s);
+// Sweep temporaries: the working vector (solver layout) and the chunk and
+// separator buffers the stage kernels address.
+struct SweepWork {
+  void* u; void* z; void* rc; void* lc; void* xs; void* ps;
+};
+// direct launches of a 2D plan's stage chain on caller-provided temporaries
+// (the plan itself is only read)
+int sweep_launch_work(const Plan& p, const SweepWork& w, int nrhs, cudaStream_t s);
 void release_sweep_graphs(Plan& p);
 // chunk length stored by hs_autotune in `path` for this key (0 if none)
 // chunk length (and separator grouping in *sep, 0 if not recorded) stored by

@@ -110,7 +110,7 @@ extern "C" int hs_default_options(hs_options* opt) {
   if (!opt) return HS_EINVAL;
   opt->alpha = 2.0;
   opt->pml_C = 20.0;
-  opt->moving_pml_C = 40.0;
+  opt->moving_pml_C = 0.0;
   opt->layers_per_step = 12;
   opt->factor_prec = HS_C64;
   opt->chunk = 0;
@@ -208,8 +208,9 @@ static int prepare_plan3d(const double* c, double omega, int n, int pml_width, i
     if (!(c[k] > 0.0) || !std::isfinite(c[k])) return HS_EINVAL;
   Plan* p = new Plan();
   p->n = n; p->dim = 3; p->bp = pml_width; p->b = moving_pml_width; p->dL = opt.layers_per_step;
-  p->omega = omega; p->alpha = opt.alpha; p->C = opt.pml_C; p->Cm = opt.moving_pml_C; p->h = 1.0 / (n + 1);
+  p->omega = omega; p->alpha = opt.alpha; p->C = opt.pml_C; p->Cm = opt.moving_pml_C > 0.0 ? opt.moving_pml_C : opt.pml_C; p->h = 1.0 / (n + 1);
   p->prec = opt.factor_prec; p->max_nrhs = opt.max_nrhs; p->opt = opt;
+  cudaGetDevice(&p->device);
   p->opt.tune_cache = nullptr;
   build_blocks(*p);
   int st = HS_OK;
@@ -291,8 +292,9 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
 
   Plan* p = new Plan();
   p->n = n; p->dim = dim; p->bp = pml_width; p->b = moving_pml_width; p->dL = opt.layers_per_step;
-  p->omega = omega; p->alpha = opt.alpha; p->C = opt.pml_C; p->Cm = opt.moving_pml_C; p->h = 1.0 / (n + 1);
+  p->omega = omega; p->alpha = opt.alpha; p->C = opt.pml_C; p->Cm = opt.moving_pml_C > 0.0 ? opt.moving_pml_C : opt.pml_C; p->h = 1.0 / (n + 1);
   p->prec = opt.factor_prec; p->max_nrhs = opt.max_nrhs; p->opt = opt;
+  cudaGetDevice(&p->device);
   build_blocks(*p);
   int Wmax = 0;
   for (auto& d : p->blocks) {

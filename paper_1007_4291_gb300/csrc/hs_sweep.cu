@@ -972,11 +972,11 @@ int run_stage(const Plan& p, SweepArgs a, cudaStream_t s) {
 }
 
 template <typename R>
-int sweep_t(Plan& p, int nrhs, cudaStream_t s) {
+int sweep_t(const Plan& p, const SweepWork& w, int nrhs, cudaStream_t s) {
   SweepArgs a{};
   a.n = p.n; a.L = p.L; a.P = p.P; a.R = nrhs;
-  a.fac = p.d_fac; a.red = p.d_red; a.u = p.d_u;
-  a.z = p.d_z; a.rc = p.d_rc; a.lc = p.d_lc; a.xs = p.d_xs; a.ps = p.d_ps;
+  a.fac = p.d_fac; a.red = p.d_red; a.u = w.u;
+  a.z = w.z; a.rc = w.rc; a.lc = w.lc; a.xs = w.xs; a.ps = w.ps;
   if (sizeof(R) == 4) { a.a2 = p.f_a2; a.inv_s1 = p.f_inv_s1; }
   else { a.a2 = p.d_a2; a.inv_s1 = p.d_inv_s1; }
   a.status = p.d_status;
@@ -1077,8 +1077,13 @@ void sweep_prepare_attributes(int prec) {
   if (prec == HS_C64) set_attrs<float>(); else set_attrs<double>();
 }
 
+int sweep_launch_work(const Plan& p, const SweepWork& w, int nrhs, cudaStream_t s) {
+  return (p.prec == HS_C64) ? sweep_t<float>(p, w, nrhs, s) : sweep_t<double>(p, w, nrhs, s);
+}
+
 int sweep_launch(Plan& p, int nrhs, cudaStream_t s) {
-  return (p.prec == HS_C64) ? sweep_t<float>(p, nrhs, s) : sweep_t<double>(p, nrhs, s);
+  const SweepWork w{p.d_u, p.d_z, p.d_rc, p.d_lc, p.d_xs, p.d_ps};
+  return sweep_launch_work(p, w, nrhs, s);
 }
 
 namespace {

@@ -18,7 +18,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 C_PML = 20.0
-C_MOVING = 40.0      # library default strength of the moving PMLs
+C_MOVING = None      # library default: the moving PMLs take the boundary C (Eq. helma reuses sigma_2)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -33,10 +33,10 @@ def relerr(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
-def plan3(c, omega, bp, b, dL, prec=hs.HS_C64, alpha=1.0, R=4, frontal=3):
+def plan3(c, omega, bp, b, dL, prec=hs.HS_C64, alpha=1.0, R=4, frontal=3, Cm=None):
     n = c.shape[0]
     o = hs.hs_default_options(alpha=alpha, pml_C=C_PML, layers_per_step=dL, factor_prec=prec, max_nrhs=R,
-                              frontal_gemm=frontal)
+                              frontal_gemm=frontal, moving_pml_C=Cm or 0.0)
     return hs.hs_setup(c.ravel(), omega, n, 3, bp, b, o)
 
 
@@ -98,6 +98,28 @@ def test_apply3_matches_oracle(case, mode):
         err = max(relerr(z[k], ref[k]) for k in range(R))
         print("3D apply n=%d prec=%d frontal=%d: max relative error %.3e" % (n, prec, frontal, err))
         assert err <= tol
+    finally:
+        hs.hs_destroy(p)
+
+
+@pytest.mark.parametrize("prec,tol", [(hs.HS_C64, 1e-4), (hs.HS_C128, 1e-10)])
+def test_apply3_separate_moving_strength(prec, tol):
+    """The opt-in moving-PML strength (2C) reaches the x3 profile of every slab."""
+    n, bp, b, dL, R = 13, 3, 3, 2, 2
+    c = I.random_velocity(n, 5, dim=3)
+    omega, alpha = 2 * np.pi * 1.5, 1.0
+    p = plan3(c, omega, bp, b, dL, prec=prec, alpha=alpha, R=R, frontal=0, Cm=2 * C_PML)
+    try:
+        r = I.random_rhs(n, R, 6, dim=3)
+        tdt = torch.complex64 if prec == hs.HS_C64 else torch.complex128
+        rg = torch.from_numpy(r).to("cuda").to(tdt)
+        zg = torch.empty_like(rg)
+        hs.hs_apply(p, rg, zg, R, prec)
+        torch.cuda.synchronize()
+        z = zg.cpu().numpy().astype(np.complex128)
+        st = H3.setup(c, omega, bp, b, dL, alpha, C_PML, Cm=2 * C_PML)
+        ref = H3.apply(st, rg.cpu().numpy().astype(np.complex128))
+        assert max(relerr(z[k], ref[k]) for k in range(R)) <= tol
     finally:
         hs.hs_destroy(p)
 

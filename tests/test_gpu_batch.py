@@ -20,7 +20,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 C_PML = 20.0
-C_MOVING = 40.0      # library default strength of the moving PMLs
+C_MOVING = None      # library default: the moving PMLs take the boundary C (Eq. helma reuses sigma_2)
 BP = 6
 
 

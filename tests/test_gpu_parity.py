@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 C_PML = 20.0
-C_MOVING = 40.0      # library default strength of the moving PMLs
+C_MOVING = None      # library default: the moving PMLs take the boundary C (Eq. helma reuses sigma_2)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -34,10 +34,10 @@ def relerr(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
-def make_plan(c, omega, bp, b, dL, prec=hs.HS_C64, chunk=0, alpha=2.0, max_nrhs=8, restart=20):
+def make_plan(c, omega, bp, b, dL, prec=hs.HS_C64, chunk=0, alpha=2.0, max_nrhs=8, restart=20, Cm=None):
     n = c.shape[0]
     o = hs.hs_default_options(alpha=alpha, pml_C=C_PML, layers_per_step=dL, factor_prec=prec, chunk=chunk,
-                              max_nrhs=max_nrhs, restart=restart)
+                              max_nrhs=max_nrhs, restart=restart, moving_pml_C=Cm or 0.0)
     return hs.hs_setup(c.ravel(), omega, n, 2, bp, b, o)
 
 
@@ -122,16 +122,17 @@ APPLY_CASES = [
 
 
 @pytest.mark.parametrize("case", APPLY_CASES)
-@pytest.mark.parametrize("prec", [hs.HS_C64, hs.HS_C128])
-def test_apply_matches_oracle(case, prec):
+@pytest.mark.parametrize("prec,Cm", [(hs.HS_C64, None), (hs.HS_C128, None), (hs.HS_C64, 2 * C_PML)])
+def test_apply_matches_oracle(case, prec, Cm):
+    """Cm None: the paper's single constant (library default); 2C: the opt-in
+    separate moving-PML strength."""
     n, bp, b, dL, chunk, R = case
     c = I.random_velocity(n, 7)
     omega, alpha = 2 * np.pi * 2.5, 2.0
-    plan = make_plan(c, omega, bp, b, dL, prec=prec, chunk=chunk, alpha=alpha)
+    plan = make_plan(c, omega, bp, b, dL, prec=prec, chunk=chunk, alpha=alpha, Cm=Cm)
     try:
         r = I.random_rhs(n, R, 5)
-        st = S.setup(c, omega, bp, b, dL, alpha, C_PML, Cm=C_MOVING)
-        ref = S.apply(st, r)
+        st = S.setup(c, omega, bp, b, dL, alpha, C_PML, Cm=Cm)
         io = hs.HS_C64 if prec == hs.HS_C64 else hs.HS_C128
         rin = r.astype(np.complex64).astype(np.complex128) if io == hs.HS_C64 else r
         ref = S.apply(st, rin)

@@ -298,3 +298,145 @@ def test_moving_pml_strength_is_a_preconditioner_parameter():
     s1 = S.window_x2_stretch(moving, n, bp, b, 20.0, omega, Cm=40.0)[0]
     s0 = S.window_x2_stretch(moving, n, bp, b, 20.0, omega)[0]
     assert not np.allclose(s0, s1) and np.allclose(s0[-dL:], 1.0) and np.allclose(s1[-dL:], 1.0)
+
+
+# ---------------------------------------------------------------- moving PML (Eq. helma)
+#
+# Hand-computed values of the moving profile.  Grid n = 47 (h = 1/48), boundary
+# PML b_p = 6, moving PML b = 4 != b_p, d = 2 rows per step, C = 20.  Eq. helma
+# shifts the one-sided profile of Eq. sigma so that it starts at the row lo - b
+# (the window's Dirichlet row) and uses eta = b h, so on the window of a lower
+# block [lo..hi] = [9..10] (window rows 6..10) the distance to the Dirichlet
+# row 5 is t = 1, 2, 3, 4, 5 grid spacings and
+#   sigma = (C / (4h)) ((t - 4)/4)^2 = (C/h) (t - 4)^2 / 64   for t <= 4, else 0.
+# The tables below hold sigma h / C in 64ths, worked out by hand, at the window
+# rows, at the half points above them (j + 1/2) and below them (j - 1/2).
+_HAND = dict(
+    n=47, bp=6, b=4, dL=2, C=20.0,
+    lower=dict(index=2, rows=(6, 10), lo=9, hi=10,
+               at=[9, 4, 1, 0, 0], up=[6.25, 2.25, 0.25, 0, 0], dn=[12.25, 6.25, 2.25, 0.25, 0]),
+    # upper block [38..39], window 38..42, Dirichlet row 43 (= hi + b)
+    upper=dict(index=2, rows=(38, 42), lo=38, hi=39,
+               at=[0, 0, 1, 4, 9], up=[0, 0.25, 2.25, 6.25, 12.25], dn=[0, 0, 0.25, 2.25, 6.25]),
+    # middle layer 24, window 21..27, Dirichlet rows 20 and 28: both profiles
+    middle=dict(rows=(21, 27), lo=24, hi=24,
+                at=[9, 4, 1, 0, 1, 4, 9], up=[6.25, 2.25, 0.25, 0.25, 2.25, 6.25, 12.25],
+                dn=[12.25, 6.25, 2.25, 0.25, 0.25, 2.25, 6.25]),
+)
+
+
+def _hand_profile_mismatches(window_stretch, Cm=None):
+    """Compare window_stretch (the 2D x2 or the 3D x3 moving stretch) with the
+    hand table; returns the list of mismatching (kind, which) pairs."""
+    g = _HAND
+    n, bp, b, dL, C = g["n"], g["bp"], g["b"], g["dL"], g["C"]
+    Cm = C if Cm is None else Cm
+    h = 1.0 / (n + 1)
+    omega = 2 * np.pi * 3.0
+    lower, upper, mid = S.partition(n, bp, b, dL)
+    blocks = dict(lower=lower[g["lower"]["index"]], upper=upper[g["upper"]["index"]], middle=mid)
+    bad = []
+    for kind, blk in blocks.items():
+        e = g[kind]
+        assert (blk.wlo, blk.whi, blk.lo, blk.hi) == (e["rows"][0], e["rows"][1], e["lo"], e["hi"])
+        got = window_stretch(blk, n, bp, b, C, omega, Cm=Cm)
+        for which, vals in zip(("at", "up", "dn"), got):
+            sig = (Cm / h) * np.array(e[which], dtype=np.float64) / 64.0
+            want = 1.0 / (1.0 + 1j * sig / omega)
+            if not np.allclose(vals, want, rtol=1e-13, atol=0):
+                bad.append((kind, which))
+    return bad
+
+
+def test_moving_profile_hand_computed_values():
+    """Eq. helma with b != b_p: s2^m at the window rows and half points of a
+    lower, an upper and the middle block equals the hand-computed table (both
+    at the paper's single constant C and at another strength), in 2D and for
+    the x3 profile of the 3D slabs."""
+    from oracle import helmholtz3d as H3
+    assert _hand_profile_mismatches(S.window_x2_stretch) == []
+    assert _hand_profile_mismatches(S.window_x2_stretch, Cm=40.0) == []
+    assert _hand_profile_mismatches(H3.window_x3_stretch) == []
+
+
+@pytest.mark.parametrize("slip", ["C_not_over_eta", "eta_from_bp", "shift_up", "shift_down"])
+def test_moving_profile_planted_slips_fail_hand_pin(monkeypatch, slip):
+    """Planted mistakes in the moving profile each break the hand table:
+    strength C instead of C/eta_b, eta_b = b_p h instead of b h, and the
+    profile shifted by one row either way."""
+    orig = S.moving_sigma
+    h = 1.0 / (_HAND["n"] + 1)
+    planted = {
+        "C_not_over_eta": lambda t, e, C: orig(t, e, C) * e,
+        "eta_from_bp": lambda t, e, C: orig(t, _HAND["bp"] * h, C),
+        "shift_up": lambda t, e, C: orig(np.asarray(t) + h, e, C),
+        "shift_down": lambda t, e, C: orig(np.asarray(t) - h, e, C),
+    }[slip]
+    monkeypatch.setattr(S, "moving_sigma", planted)
+    assert _hand_profile_mismatches(S.window_x2_stretch) != []
+
+
+# Physics of the moving PML (Sec. 2.2): T_m, the (m, m) block of the inverse of
+# A_alpha restricted to the half space of rows 1..m (zero Dirichlet values on
+# row m + 1), is the discrete half-space Green's function on row m; T~_m
+# replaces everything below row m - b + 1 by a PML of b rows.  For constant
+# velocity the approximation must improve as b grows and be close at b = 12
+# (the paper's width).  The reference T_m is a sparse direct solve of the
+# truncated operator, independent of the window and band code.
+_GREEN = dict(n=95, bp=12, alpha=2.0, C=20.0, widths=(4, 8, 12), bounds=(5e-3, 4e-4, 1e-4))
+
+
+def _half_space_errors(kind):
+    import scipy.sparse.linalg as spla_
+    g = _GREEN
+    n, bp, al, C = g["n"], g["bp"], g["alpha"], g["C"]
+    omega = 2 * np.pi * (n + 1) / 16.0          # 16 points per wavelength
+    c = I.constant_velocity(n)
+    A = H.helmholtz_matrix(c, omega, bp, C, al).tocsc()
+    h = 1.0 / (n + 1)
+    x = h * np.arange(1, n + 1)
+    gsrc = np.exp(-((x - 0.5) / 0.05) ** 2).astype(np.complex128)   # smooth load on row m
+    m = (n + 1) // 2 - 4 if kind == "lower" else (n + 1) // 2 + 4
+    if kind == "lower":
+        sub = np.arange(0, m * n)                   # rows 1..m
+        pos = slice((m - 1) * n, m * n)
+    else:
+        sub = np.arange((m - 1) * n, n * n)         # rows m..n
+        pos = slice(0, n)
+    lu = spla_.splu(A[sub][:, sub].tocsc())
+    rhs = np.zeros(sub.size, dtype=np.complex128)
+    rhs[pos] = gsrc
+    exact = lu.solve(rhs)[pos]
+    errs = []
+    for b in g["widths"]:
+        blk = S.Block(kind, m, m, m - b + 1 if kind == "lower" else m, m if kind == "lower" else m + b - 1)
+        approx = S.factor_block(blk, c, omega, bp, b, C, al).t_tilde(gsrc.reshape(1, 1, n))[0, 0]
+        errs.append(np.linalg.norm(approx - exact) / np.linalg.norm(exact))
+    return errs
+
+
+def _half_space_pin_holds(errs):
+    return all(e < bound for e, bound in zip(errs, _GREEN["bounds"])) and errs[0] > errs[1] > errs[2]
+
+
+@pytest.mark.parametrize("kind", ["lower", "upper"])
+def test_moving_pml_approximates_half_space_green_function(kind):
+    """||T~_m g - T_m g|| / ||T_m g|| falls as the moving PML widens
+    (b = 4, 8, 12) and is below 1e-4 at b = 12, for both fronts."""
+    errs = _half_space_errors(kind)
+    assert _half_space_pin_holds(errs), errs
+
+
+@pytest.mark.parametrize("slip", ["C_not_over_eta", "eta_from_bp", "shift_up", "shift_down"])
+def test_moving_pml_planted_slips_fail_green_pin(monkeypatch, slip):
+    """The same planted slips of the profile also break the half-space pin."""
+    orig = S.moving_sigma
+    h = 1.0 / (_GREEN["n"] + 1)
+    planted = {
+        "C_not_over_eta": lambda t, e, C: orig(t, e, C) * e,
+        "eta_from_bp": lambda t, e, C: orig(t, _GREEN["bp"] * h, C),
+        "shift_up": lambda t, e, C: orig(np.asarray(t) + h, e, C),
+        "shift_down": lambda t, e, C: orig(np.asarray(t) - h, e, C),
+    }[slip]
+    monkeypatch.setattr(S, "moving_sigma", planted)
+    assert not _half_space_pin_holds(_half_space_errors("lower"))
