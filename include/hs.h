@@ -86,6 +86,18 @@ typedef struct {
   int sep_rhs_per_cta;   /* RHS per CTA of the separator solve (phase 2 of every sweep stage):
                             0 picks one while the RHS of both fronts fit on the SMs one CTA each,
                             else two or four; 1, 2 or 4 fix it (complex128 factors: at most two). default 0 */
+  int two_front;         /* 1: PML on all four sides, two fronts sweeping toward the middle layer
+                            (Sec. 2.3, every experiment of the paper).  0 (2D only): the formulation
+                            of Sec. 2.1-2.2 and Algorithms 3-4 as printed: zero Dirichlet values at
+                            x2 = 1, the one-sided sigma_2 of Eq. sigma at x2 = 0, one upward sweep
+                            from the front F; the operator A changes accordingly (hs_matvec and
+                            hs_solve use it), and n may be even.                        default 1 */
+  int buffer_rows;       /* k >= 0 rows between each block and its moving PML (Sec. 2.2, the
+                            buffer layers): window [lo - k - b + 1, hi] (mirrored for the upper
+                            front, both sides for the middle layer).  A window that would cross
+                            the grid boundary is cut there and keeps the operator's own profile
+                            (the exact Schur inverse).  2D only; windows must stay <= 32 rows.
+                                                                                           default 0 */
 } hs_options;
 
 typedef struct hs_plan hs_plan;

@@ -36,22 +36,34 @@ def pml_sigma(t, eta, C):
     return out
 
 
+def pml_sigma_one_sided(t, eta, C):
+    """sigma_2 of Eq. sigma: the quadratic ramp near x2 = 0 only (the
+    Dirichlet-top formulation of Sec. 2.1), zero on [eta, 1]."""
+    t = np.asarray(t, dtype=np.float64)
+    out = np.zeros_like(t)
+    lo = t <= eta
+    out[lo] = (C / eta) * ((t[lo] - eta) / eta) ** 2
+    return out
+
+
 def stretch(sigma, omega):
     """s = (1 + i sigma/omega)^(-1) (Sec. 2.1)."""
     return 1.0 / (1.0 + 1j * np.asarray(sigma) / omega)
 
 
-def axis_stretch(n, bp, C, omega):
+def axis_stretch(n, bp, C, omega, one_sided=False):
     """Stretch factors of one axis at integer points k h (k = 0..n+1) and at
-    half points (k + 1/2) h (k = 0..n).  eta = bp*h is the boundary PML width.
+    half points (k + 1/2) h (k = 0..n).  eta = bp*h is the boundary PML width;
+    ``one_sided`` takes sigma_2 of Eq. sigma (PML at 0 only).
 
     Returns (s_int, s_half) with s_int[k] = s(k h), s_half[k] = s((k+1/2) h).
     """
     h = 1.0 / (n + 1)
     eta = bp * h
+    sig = pml_sigma_one_sided if one_sided else pml_sigma
     k = np.arange(n + 2, dtype=np.float64)
-    s_int = stretch(pml_sigma(k * h, eta, C), omega)
-    s_half = stretch(pml_sigma((k[: n + 1] + 0.5) * h, eta, C), omega)
+    s_int = stretch(sig(k * h, eta, C), omega)
+    s_half = stretch(sig((k[: n + 1] + 0.5) * h, eta, C), omega)
     return s_int, s_half
 
 
@@ -83,20 +95,22 @@ def row_coefficients(c_rows, omega, alpha, h, s1, s2_int, s2_up, s2_dn):
     return dict(E=E, W=W, N=N, S=S, D=D)
 
 
-def stencil_coefficients(c, omega, bp, C, alpha=0.0):
+def stencil_coefficients(c, omega, bp, C, alpha=0.0, dirichlet_top=False):
     """Coefficients of Eq. helmd on the full grid.
 
     ``c`` is the (n, n) velocity array indexed [j-1, i-1] (row j = x2 index,
     column i = x1 index).  Returns a dict of (n, n) complex arrays
     E, W, N, S (couplings to (i+1,j), (i-1,j), (i,j+1), (i,j-1)) and D (the
-    diagonal of A_alpha; alpha = 0 gives A).
+    diagonal of A_alpha; alpha = 0 gives A).  ``dirichlet_top``: the
+    formulation of Sec. 2.1 (sigma_2 one-sided, no PML at x2 = 1; the zero
+    Dirichlet values outside the grid are the boundary condition there).
     """
     c = np.asarray(c, dtype=np.float64)
     n = c.shape[0]
     assert c.shape == (n, n)
     h = 1.0 / (n + 1)
     s1 = axis_stretch(n, bp, C, omega)
-    s2_int, s2_half = axis_stretch(n, bp, C, omega)
+    s2_int, s2_half = axis_stretch(n, bp, C, omega, one_sided=dirichlet_top)
     j = np.arange(1, n + 1)
     return row_coefficients(c, omega, alpha, h, s1, s2_int[j], s2_half[j], s2_half[j - 1])
 
@@ -121,9 +135,9 @@ def assemble(coef):
     return A
 
 
-def helmholtz_matrix(c, omega, bp, C, alpha=0.0):
+def helmholtz_matrix(c, omega, bp, C, alpha=0.0, dirichlet_top=False):
     """A (alpha = 0) or A_alpha of Eq. helmd / Eq. helmalpha as a CSR matrix."""
-    return assemble(stencil_coefficients(c, omega, bp, C, alpha))
+    return assemble(stencil_coefficients(c, omega, bp, C, alpha, dirichlet_top))
 
 
 def apply_stencil(coef, x):

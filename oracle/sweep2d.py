@@ -51,6 +51,7 @@ class Block:
     hi: int        # last row of the block
     wlo: int       # first row of the subproblem window
     whi: int       # last row of the subproblem window
+    exact: bool = False   # window cut at the grid boundary: the operator's own profile
 
     @property
     def rows(self):
@@ -61,7 +62,49 @@ class Block:
         return self.whi - self.wlo + 1
 
 
-def partition(n, bp, b, dL, full_window=False):
+def _lower_window(lo, hi, b, k, full_window):
+    """Window of a lower-front block with k buffer rows between the block and
+    its moving PML (Sec. 2.2): [lo - k - b + 1, hi]; cut at row 1 when it
+    would cross the boundary, where the window keeps the operator's own
+    profile (an exact Schur inverse, as for the paper's first layers)."""
+    if full_window:
+        return Block("lower", lo, hi, 1, hi)
+    wlo = lo - k - b + 1
+    return Block("lower", lo, hi, max(wlo, 1), hi, exact=wlo < 1)
+
+
+def _upper_window(lo, hi, b, k, n, full_window):
+    if full_window:
+        return Block("upper", lo, hi, lo, n)
+    whi = hi + k + b - 1
+    return Block("upper", lo, hi, lo, min(whi, n), exact=whi > n)
+
+
+def partition_single(n, bp, b, dL, full_window=False, buffer=0):
+    """Single-front partition of Sec. 2.1-2.2 (the formulation with a zero
+    Dirichlet condition at x2 = 1 and the PML at x2 = 0 only): the front
+    F = rows 1..bp, then blocks of d rows swept upward to the top row n, the
+    last one taking the remainder (Algorithm 3 with d layers per step, Sec.
+    2.3).  Every block's window is its rows plus b - 1 rows below; the top
+    block's window ends at row n, next to the Dirichlet boundary.
+
+    Returns (lower, [], None): the blocks in sweep order, no second front and
+    no middle layer.
+    """
+    if n < bp + 1 or bp < 1 or dL < 1 or b < 1 or b > bp + 1:
+        raise ValueError("invalid partition parameters")
+    rows = n - bp
+    sizes = [dL] * (rows // dL) + ([rows % dL] if rows % dL else [])
+    lower = [Block("F", 1, bp, 1, bp)]
+    lo = bp + 1
+    for d in sizes:
+        hi = lo + d - 1
+        lower.append(_lower_window(lo, hi, b, buffer, full_window))
+        lo = hi + 1
+    return lower, [], None
+
+
+def partition(n, bp, b, dL, full_window=False, buffer=0):
     """Two-front block partition of Sec. 2.3 (Fig. 2 left and right).
 
     The fronts sweep from F = rows 1..bp upward and from E = rows
@@ -75,10 +118,13 @@ def partition(n, bp, b, dL, full_window=False):
     order, ``upper`` = [E, B'_1, ..., B'_K], ``middle`` = the middle layer.
     With ``full_window`` every window extends to the domain boundary on its
     eliminated side (exact-limit test knob: then T~_B equals the exact Schur
-    inverse, Sec. 2.2).
+    inverse, Sec. 2.2).  ``buffer`` = k rows between each block and its
+    moving PML (Sec. 2.2, windows as in ``_lower_window``).
     """
     if n % 2 != 1 or n < 2 * bp + 1 or bp < 1 or dL < 1 or b < 1 or b > bp + 1:
         raise ValueError("invalid partition parameters")
+    if (n + 1) // 2 - buffer - b < 0:
+        raise ValueError("the middle layer's window does not fit")
     rows_front = (n - 1) // 2 - bp
     sizes = [dL] * (rows_front // dL) + ([rows_front % dL] if rows_front % dL else [])
     lower = [Block("F", 1, bp, 1, bp)]
@@ -86,15 +132,15 @@ def partition(n, bp, b, dL, full_window=False):
     lo = bp + 1
     for d in sizes:
         hi = lo + d - 1
-        lower.append(Block("lower", lo, hi, 1 if full_window else lo - b + 1, hi))
+        lower.append(_lower_window(lo, hi, b, buffer, full_window))
         ulo, uhi = n + 1 - hi, n + 1 - lo
-        upper.append(Block("upper", ulo, uhi, ulo, n if full_window else uhi + b - 1))
+        upper.append(_upper_window(ulo, uhi, b, buffer, n, full_window))
         lo = hi + 1
     m = (n + 1) // 2
     if full_window:
         middle = Block("middle", m, m, 1, n)
     else:
-        middle = Block("middle", m, m, m - b + 1, m + b - 1)
+        middle = Block("middle", m, m, m - buffer - b + 1, m + buffer + b - 1)
     return lower, upper, middle
 
 
@@ -108,31 +154,34 @@ def moving_sigma(t, eta_b, C):
     return out
 
 
-def window_x2_stretch(blk, n, bp, b, C, omega, full_window=False, Cm=None):
+def window_x2_stretch(blk, n, bp, b, C, omega, full_window=False, Cm=None, dirichlet_top=False):
     """x2 stretch of H_B on the window rows and at the half points.
 
     Returns (s_int, s_up, s_dn) of length w: s2 at rows wlo..whi, at (j+1/2)
     and at (j-1/2).  F, E and full-window blocks use the original boundary
-    profile (strength C, part of A); moving blocks use the moving profile of
-    Eq. helma with strength Cm (a parameter of the preconditioner only;
-    None = C).
+    profile (strength C, part of A; one-sided sigma_2 for the Dirichlet-top
+    formulation); moving blocks use the moving profile of Eq. helma with
+    strength Cm (a parameter of the preconditioner only; None = C).
     """
     Cm = C if Cm is None else Cm
     h = 1.0 / (n + 1)
     j = np.arange(blk.wlo, blk.whi + 1, dtype=np.float64)
-    if blk.kind in ("F", "E") or full_window:
+    if blk.kind in ("F", "E") or full_window or blk.exact:
         eta = bp * h
-        sig = lambda x: H.pml_sigma(x, eta, C)
+        prof = H.pml_sigma_one_sided if dirichlet_top else H.pml_sigma
+        sig = lambda x: prof(x, eta, C)
     else:
+        # the profile starts at the window's Dirichlet row(s) just outside it:
+        # row lo - k - b below a lower block, hi + k + b above an upper one
         eta_b = b * h
         if blk.kind == "lower":
-            d0 = blk.lo - b
+            d0 = blk.wlo - 1
             sig = lambda x: moving_sigma(x - d0 * h, eta_b, Cm)
         elif blk.kind == "upper":
-            d1 = blk.hi + b
+            d1 = blk.whi + 1
             sig = lambda x: moving_sigma(d1 * h - x, eta_b, Cm)
         else:
-            d0, d1 = blk.lo - b, blk.hi + b
+            d0, d1 = blk.wlo - 1, blk.whi + 1
             sig = lambda x: moving_sigma(x - d0 * h, eta_b, Cm) + moving_sigma(d1 * h - x, eta_b, Cm)
     s_int = H.stretch(sig(j * h), omega)
     s_up = H.stretch(sig((j + 0.5) * h), omega)
@@ -140,12 +189,12 @@ def window_x2_stretch(blk, n, bp, b, C, omega, full_window=False, Cm=None):
     return s_int, s_up, s_dn
 
 
-def window_coefficients(blk, c, omega, bp, b, C, alpha, full_window=False, Cm=None):
+def window_coefficients(blk, c, omega, bp, b, C, alpha, full_window=False, Cm=None, dirichlet_top=False):
     """Eq. helmd coefficients of H_B (Eq. helma discretised on the window)."""
     n = c.shape[0]
     h = 1.0 / (n + 1)
     s1 = H.axis_stretch(n, bp, C, omega)
-    s_int, s_up, s_dn = window_x2_stretch(blk, n, bp, b, C, omega, full_window, Cm)
+    s_int, s_up, s_dn = window_x2_stretch(blk, n, bp, b, C, omega, full_window, Cm, dirichlet_top)
     rows = np.arange(blk.wlo, blk.whi + 1)
     return H.row_coefficients(c[rows - 1, :], omega, alpha, h, s1, s_int, s_up, s_dn)
 
@@ -204,9 +253,9 @@ class FactoredBlock:
         return np.transpose(x[:, :, off:off + (blk.hi - blk.lo + 1)], (0, 2, 1)).copy()
 
 
-def factor_block(blk, c, omega, bp, b, C, alpha, full_window=False, Cm=None):
+def factor_block(blk, c, omega, bp, b, C, alpha, full_window=False, Cm=None, dirichlet_top=False):
     """One step of Algorithm 3: LU of P_B H_B P_B^t (LAPACK band LU)."""
-    coef = window_coefficients(blk, c, omega, bp, b, C, alpha, full_window, Cm)
+    coef = window_coefficients(blk, c, omega, bp, b, C, alpha, full_window, Cm, dirichlet_top)
     ab, kl, ku = band_matrix_x2_first(coef)
     lu, ipiv, info = lapack.zgbtrf(ab, kl, ku)
     if info != 0:
@@ -223,15 +272,21 @@ class Setup:
     Ncoup: np.ndarray      # N_{i,j} of A: coupling (i,j) -> (i,j+1), shape (n, n) [j-1, i-1]
 
 
-def setup(c, omega, bp, b, dL, alpha, C, full_window=False, Cm=None):
-    """Algorithm 3 (two-front, d layers per step): factor every block.
-    Cm: strength of the moving PMLs (None = C)."""
+def setup(c, omega, bp, b, dL, alpha, C, full_window=False, Cm=None, two_front=True, buffer=0):
+    """Algorithm 3 (d layers per step): factor every block.  Cm: strength of
+    the moving PMLs (None = C).  ``two_front`` False: the single-front
+    Dirichlet-top formulation of Sec. 2.1-2.2 (one-sided sigma_2, one
+    upward sweep, no middle layer).  ``buffer``: k rows between each block
+    and its moving PML (Sec. 2.2)."""
     c = np.asarray(c, dtype=np.float64)
     n = c.shape[0]
-    lower, upper, middle = partition(n, bp, b, dL, full_window)
-    f = lambda blk: factor_block(blk, c, omega, bp, b, C, alpha, full_window, Cm)
-    coef = H.stencil_coefficients(c, omega, bp, C, alpha)
-    return Setup(n, [f(B) for B in lower], [f(B) for B in upper], f(middle), coef["N"])
+    top = not two_front
+    lower, upper, middle = (partition(n, bp, b, dL, full_window, buffer) if two_front
+                            else partition_single(n, bp, b, dL, full_window, buffer))
+    f = lambda blk: factor_block(blk, c, omega, bp, b, C, alpha, full_window, Cm, top)
+    coef = H.stencil_coefficients(c, omega, bp, C, alpha, dirichlet_top=top)
+    return Setup(n, [f(B) for B in lower], [f(B) for B in upper], f(middle) if middle is not None else None,
+                 coef["N"])
 
 
 def apply(st, r):
@@ -245,22 +300,30 @@ def apply(st, r):
     Nc = st.Ncoup
     rows = lambda B: slice(B.blk.lo - 1, B.blk.hi)
     v = {}
+    n = st.n
     # forward sweep, lower front: u_{hi+1} -= A_{hi+1,hi} (T~_B u_B)_{hi}
+    # (single front: the top block has no row above it)
     for k, B in enumerate(st.lower):
         v[k, 0] = B.t_tilde(u[:, rows(B), :])
         hi = B.blk.hi
-        u[:, hi, :] -= Nc[hi - 1, :] * v[k, 0][:, -1, :]
+        if hi < n:
+            u[:, hi, :] -= Nc[hi - 1, :] * v[k, 0][:, -1, :]
     # forward sweep, upper front: u_{lo-1} -= A_{lo-1,lo} (T~_B u_B)_{lo}
     for k, B in enumerate(st.upper):
         v[k, 1] = B.t_tilde(u[:, rows(B), :])
         lo = B.blk.lo
         u[:, lo - 2, :] -= Nc[lo - 2, :] * v[k, 1][:, 0, :]
     # middle block with moving PMLs on both sides
-    u[:, rows(st.middle), :] = st.middle.t_tilde(u[:, rows(st.middle), :])
-    # backward sweep, lower front: u_B = v_B - T~_B (A_{B,hi+1} u_{hi+1})
+    if st.middle is not None:
+        u[:, rows(st.middle), :] = st.middle.t_tilde(u[:, rows(st.middle), :])
+    # backward sweep, lower front: u_B = v_B - T~_B (A_{B,hi+1} u_{hi+1});
+    # the single front's top block keeps u_B = v_B (Algorithm 4)
     for k in range(len(st.lower) - 1, -1, -1):
         B = st.lower[k]
         hi = B.blk.hi
+        if hi == n:
+            u[:, rows(B), :] = v[k, 0]
+            continue
         g = np.zeros_like(v[k, 0])
         g[:, -1, :] = Nc[hi - 1, :] * u[:, hi, :]
         u[:, rows(B), :] = v[k, 0] - B.t_tilde(g)
@@ -325,4 +388,41 @@ def exact_apply(ex, f):
             nxt = front[k + 1] if k + 1 < len(front) else ex["middle"]
             I, J = idx(B), idx(nxt)
             u[I] -= T[B.lo] @ (A[np.ix_(I, J)] @ u[J])
+    return u.reshape(n, n)
+
+
+def exact_setup_single(c, omega, bp, b, dL, alpha, C):
+    """Algorithm 1 in the single-front order of the Dirichlet-top formulation
+    (Sec. 2.1): S_F = A_FF, S_m = A_mm - A_{m,m-1} T_{m-1} A_{m-1,m},
+    T_m = S_m^{-1}, blocks of d rows upward to row n.  Tiny n only."""
+    c = np.asarray(c, dtype=np.float64)
+    n = c.shape[0]
+    A = H.helmholtz_matrix(c, omega, bp, C, alpha, dirichlet_top=True).toarray()
+    blocks, _, _ = partition_single(n, bp, b, dL)
+    idx = lambda B: np.arange((B.lo - 1) * n, B.hi * n)
+    T = []
+    for k, B in enumerate(blocks):
+        I = idx(B)
+        S = A[np.ix_(I, I)].copy()
+        if k > 0:
+            P = idx(blocks[k - 1])
+            S -= A[np.ix_(I, P)] @ T[k - 1] @ A[np.ix_(P, I)]
+        T.append(np.linalg.inv(S))
+    return dict(n=n, A=A, T=T, blocks=blocks)
+
+
+def exact_apply_single(ex, f):
+    """Algorithm 2 in the single-front order: u = A^{-1} f exactly."""
+    n, A, T, blocks = ex["n"], ex["A"], ex["T"], ex["blocks"]
+    idx = lambda B: np.arange((B.lo - 1) * n, B.hi * n)
+    u = np.array(f, dtype=np.complex128).reshape(-1).copy()
+    for k in range(len(blocks) - 1):
+        I, J = idx(blocks[k]), idx(blocks[k + 1])
+        u[J] -= A[np.ix_(J, I)] @ (T[k] @ u[I])
+    for k, B in enumerate(blocks):
+        I = idx(B)
+        u[I] = T[k] @ u[I]
+    for k in range(len(blocks) - 2, -1, -1):
+        I, J = idx(blocks[k]), idx(blocks[k + 1])
+        u[I] -= T[k] @ (A[np.ix_(I, J)] @ u[J])
     return u.reshape(n, n)

@@ -67,6 +67,8 @@ struct BlockDesc {
   long long red_off; // offset of the reduced (separator) system factors
   long long cor_off; // offset of the corner blocks used to build the reduced system
   int s2_off;        // offset (complex elements) of the window x2 tables (3*w values)
+  int exact;         // 1: the window reaches the grid boundary on the eliminated side and keeps the
+                     // operator's own x2 profile (T~_B is then the exact Schur inverse)
 };
 
 // ---------------------------------------------------------------- plan
@@ -123,7 +125,10 @@ inline void note_launch(long long k = 1) { g_launches.fetch_add(k, std::memory_o
 #define HS_CUDA_TRY(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) return hs::cuda_status(_e); } while (0)
 
 int padded_width(int w);   // 8, 12, 16, 24, 32 or -1
-// two-front block partition of Sec. 2.3 (rows in 2D, x3 layers in 3D) into p.blocks/stages/middle
+// block partition (rows in 2D, x3 layers in 3D) into p.blocks/stages/middle:
+// two fronts (Sec. 2.3), or in 2D the single upward front of Sec. 2.1-2.2
+// whose top block takes the place of the middle layer; buffer rows (Sec. 2.2)
+// between each block and its moving PML
 void build_blocks(Plan& p);
 
 // Capture the launches body(stream) makes on `cap` into an executable graph.

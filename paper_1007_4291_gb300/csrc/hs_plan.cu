@@ -39,6 +39,11 @@ double sigma_boundary(double t, double eta, double C) {
   if (t >= 1.0 - eta) { double q = (t - 1.0 + eta) / eta; return (C / eta) * q * q; }
   return 0.0;
 }
+// sigma_2 of Eq. sigma: the ramp at t = 0 only (Dirichlet-top formulation).
+double sigma_one_sided(double t, double eta, double C) {
+  if (t <= eta) { double q = (t - eta) / eta; return (C / eta) * q * q; }
+  return 0.0;
+}
 // One-sided moving profile of Eq. helma: distance d from the window's
 // Dirichlet row, width eta_b; zero from depth eta_b on.
 double sigma_moving(double d, double eta_b, double C) {
@@ -66,34 +71,62 @@ template <typename T> int dalloc(Plan& p, T** ptr, size_t count) {
 
 // Two-front partition: F, d-row lower blocks (last one takes the remainder),
 // the middle layer (n+1)/2, and the mirrored upper front ending at E.
+// Single front (Dirichlet top, Sec. 2.1-2.2): F, then d-row blocks upward to
+// row n; the top block is solved once like the middle layer (it has no block
+// above it to correct it in the backward sweep).  With k buffer rows the
+// moving PML of a block sits k rows away from it (Sec. 2.2): window
+// [lo - k - b + 1, hi] (lower) or [lo, hi + k + b - 1] (upper); a window that
+// would cross the grid boundary is cut there and keeps the operator's own
+// profile (the exact Schur inverse, as for the first layers of the paper).
 void build_blocks(Plan& p) {
   const int n = p.n, bp = p.bp, b = p.b, dL = p.dL;
-  const int m = (n + 1) / 2;
-  const int rows_front = (n - 1) / 2 - bp;
-  std::vector<int> sizes;
-  for (int r = rows_front; r > 0; r -= std::min(dL, r)) sizes.push_back(std::min(dL, r));
+  const int kb = p.opt.buffer_rows;
   p.blocks.clear();
   p.stages.clear();
   auto add = [&](BlockDesc d) { p.blocks.push_back(d); return (int)p.blocks.size() - 1; };
+  auto lower_block = [&](int lo, int hi) {
+    BlockDesc Lb{}; Lb.kind = BK_LOWER; Lb.lo = lo; Lb.hi = hi; Lb.whi = hi;
+    Lb.wlo = lo - kb - b + 1;
+    if (Lb.wlo < 1) { Lb.wlo = 1; Lb.exact = 1; }
+    Lb.prev_lo_row = lo - 1; Lb.prev_hi_row = 0; Lb.next_row = hi < n ? hi + 1 : 0; Lb.coup_local = hi - Lb.wlo;
+    return Lb;
+  };
   BlockDesc F{}; F.kind = BK_F; F.lo = 1; F.hi = bp; F.wlo = 1; F.whi = bp;
   F.prev_lo_row = 0; F.prev_hi_row = 0; F.next_row = bp + 1; F.coup_local = bp - 1;
-  BlockDesc E{}; E.kind = BK_E; E.lo = n - bp + 1; E.hi = n; E.wlo = n - bp + 1; E.whi = n;
-  E.prev_lo_row = 0; E.prev_hi_row = 0; E.next_row = n - bp; E.coup_local = 0;
-  p.stages.push_back({add(F), add(E)});
-  int lo = bp + 1;
-  for (int d : sizes) {
-    int hi = lo + d - 1;
-    BlockDesc Lb{}; Lb.kind = BK_LOWER; Lb.lo = lo; Lb.hi = hi; Lb.wlo = lo - b + 1; Lb.whi = hi;
-    Lb.prev_lo_row = lo - 1; Lb.prev_hi_row = 0; Lb.next_row = hi + 1; Lb.coup_local = hi - Lb.wlo;
-    int ulo = n + 1 - hi, uhi = n + 1 - lo;
-    BlockDesc Ub{}; Ub.kind = BK_UPPER; Ub.lo = ulo; Ub.hi = uhi; Ub.wlo = ulo; Ub.whi = uhi + b - 1;
-    Ub.prev_lo_row = 0; Ub.prev_hi_row = uhi + 1; Ub.next_row = ulo - 1; Ub.coup_local = 0;
-    p.stages.push_back({add(Lb), add(Ub)});
-    lo = hi + 1;
+  if (!p.opt.two_front) {
+    std::vector<int> sizes;
+    for (int r = n - bp; r > 0; r -= std::min(dL, r)) sizes.push_back(std::min(dL, r));
+    p.stages.push_back({add(F)});
+    int lo = bp + 1;
+    for (size_t q = 0; q < sizes.size(); ++q) {
+      const int hi = lo + sizes[q] - 1;
+      if (q + 1 < sizes.size()) p.stages.push_back({add(lower_block(lo, hi))});
+      else p.middle = add(lower_block(lo, hi));
+      lo = hi + 1;
+    }
+  } else {
+    const int m = (n + 1) / 2;
+    const int rows_front = (n - 1) / 2 - bp;
+    std::vector<int> sizes;
+    for (int r = rows_front; r > 0; r -= std::min(dL, r)) sizes.push_back(std::min(dL, r));
+    BlockDesc E{}; E.kind = BK_E; E.lo = n - bp + 1; E.hi = n; E.wlo = n - bp + 1; E.whi = n;
+    E.prev_lo_row = 0; E.prev_hi_row = 0; E.next_row = n - bp; E.coup_local = 0;
+    p.stages.push_back({add(F), add(E)});
+    int lo = bp + 1;
+    for (int d : sizes) {
+      int hi = lo + d - 1;
+      BlockDesc Lb = lower_block(lo, hi);
+      int ulo = n + 1 - hi, uhi = n + 1 - lo;
+      BlockDesc Ub{}; Ub.kind = BK_UPPER; Ub.lo = ulo; Ub.hi = uhi; Ub.wlo = ulo; Ub.whi = uhi + kb + b - 1;
+      if (Ub.whi > n) { Ub.whi = n; Ub.exact = 1; }
+      Ub.prev_lo_row = 0; Ub.prev_hi_row = uhi + 1; Ub.next_row = ulo - 1; Ub.coup_local = 0;
+      p.stages.push_back({add(Lb), add(Ub)});
+      lo = hi + 1;
+    }
+    BlockDesc M{}; M.kind = BK_MIDDLE; M.lo = m; M.hi = m; M.wlo = m - kb - b + 1; M.whi = m + kb + b - 1;
+    M.prev_lo_row = m - 1; M.prev_hi_row = m + 1; M.next_row = 0; M.coup_local = -1;
+    p.middle = add(M);
   }
-  BlockDesc M{}; M.kind = BK_MIDDLE; M.lo = m; M.hi = m; M.wlo = m - b + 1; M.whi = m + b - 1;
-  M.prev_lo_row = m - 1; M.prev_hi_row = m + 1; M.next_row = 0; M.coup_local = -1;
-  p.middle = add(M);
   for (auto& d : p.blocks) {
     d.w = d.whi - d.wlo + 1;
     d.W = padded_width(d.w);
@@ -124,6 +157,8 @@ extern "C" int hs_default_options(hs_options* opt) {
   opt->inner_tol = 1e-4;
   opt->tune_cache = nullptr;
   opt->sep_rhs_per_cta = 0;
+  opt->two_front = 1;
+  opt->buffer_rows = 0;
   return HS_OK;
 }
 
@@ -203,6 +238,7 @@ static int prepare_plan3d(const double* c, double omega, int n, int pml_width, i
     return HS_EINVAL;
   if (opt.factor_prec != HS_C64 && opt.factor_prec != HS_C128) return HS_EINVAL;
   if (opt.frontal_gemm != 0 && opt.frontal_gemm != 1 && opt.frontal_gemm != 3) return HS_EINVAL;
+  if (opt.two_front != 1 || opt.buffer_rows != 0) return HS_EUNSUPPORTED;   // 3D: two fronts, no buffers
   const size_t N3 = (size_t)n * n * n;
   for (size_t k = 0; k < N3; ++k)
     if (!(c[k] > 0.0) || !std::isfinite(c[k])) return HS_EINVAL;
@@ -273,12 +309,20 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
   if (!c || !(omega > 0.0) || !std::isfinite(omega)) return HS_EINVAL;
   if (dim != 2 && dim != 3) return HS_EINVAL;
   if (dim == 3) return prepare_plan3d(c, omega, n, pml_width, moving_pml_width, opt_in, out);
-  if (n < 3 || n % 2 != 1 || pml_width < 1 || 2 * pml_width + 1 > n) return HS_EINVAL;
-  if (moving_pml_width < 1 || moving_pml_width > pml_width + 1) return HS_EINVAL;
-  if (n > 32767) return HS_EUNSUPPORTED;   // point indices are 32-bit (n^2 < 2^30)
   hs_options opt;
   hs_default_options(&opt);
   if (opt_in) opt = *opt_in;
+  if (opt.two_front != 0 && opt.two_front != 1) return HS_EINVAL;
+  if (opt.buffer_rows < 0) return HS_EINVAL;
+  if (opt.two_front) {
+    if (n < 3 || n % 2 != 1 || pml_width < 1 || 2 * pml_width + 1 > n) return HS_EINVAL;
+    // the middle layer's window must fit inside the grid
+    if ((n + 1) / 2 - opt.buffer_rows - moving_pml_width < 0) return HS_EINVAL;
+  } else {
+    if (n < 3 || pml_width < 1 || pml_width + 1 > n) return HS_EINVAL;
+  }
+  if (moving_pml_width < 1 || moving_pml_width > pml_width + 1) return HS_EINVAL;
+  if (n > 32767) return HS_EUNSUPPORTED;   // point indices are 32-bit (n^2 < 2^30)
   if (!(opt.alpha >= 0.0) || !(opt.pml_C >= 0.0) || !(opt.moving_pml_C >= 0.0) || opt.layers_per_step < 1 || opt.max_nrhs < 1 ||
       opt.max_nrhs > 4096 || opt.restart < 1 || opt.chunk < 0 || opt.chunk == 1 || opt.spin_budget < 1)
     return HS_EINVAL;
@@ -331,23 +375,33 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
   auto fail = [&](int s) { free_plan_memory(p); delete p; return s; };
   const double h = p->h, eta = p->bp * h, eta_b = p->b * h, C = p->C, Cm = p->Cm;
 
-  // ---- 1D tables of the x1 and x2 axes (Eq. sigma, both axes two-sided)
-  std::vector<c128> inv_s(n + 2), a_half(n + 1);
-  std::vector<c64> f_inv_s(n + 2), f_a_half(n + 1);
-  std::vector<unsigned char> pml(n + 2, 0);
-  for (int k = 0; k <= n + 1; ++k) {
-    zc v = inv_stretch(sigma_boundary(k * h, eta, C), omega);
-    inv_s[k] = to_c(v); f_inv_s[k] = to_f(v);
-  }
-  for (int k = 0; k <= n; ++k) {
-    zc v = stretch(sigma_boundary((k + 0.5) * h, eta, C), omega) / (h * h);
-    a_half[k] = to_c(v); f_a_half[k] = to_f(v);
-  }
-  for (int k = 1; k <= n; ++k) {
-    bool t = sigma_boundary(k * h, eta, C) != 0.0 || sigma_boundary((k - 0.5) * h, eta, C) != 0.0 ||
-             sigma_boundary((k + 0.5) * h, eta, C) != 0.0;
-    pml[k] = t ? 1 : 0;
-  }
+  // ---- 1D tables of the x1 and x2 axes (Eq. sigma: two-sided in x1; in x2
+  //      two-sided, or the one-sided sigma_2 for the Dirichlet-top formulation)
+  const bool top = !opt.two_front;
+  auto sig_axis = [&](int axis, double t) {
+    return (axis == 2 && top) ? sigma_one_sided(t, eta, C) : sigma_boundary(t, eta, C);
+  };
+  std::vector<c128> inv_s(n + 2), a_half(n + 1), inv_s2(n + 2), a_half2(n + 1);
+  std::vector<c64> f_inv_s(n + 2), f_a_half(n + 1), f_inv_s2(n + 2), f_a_half2(n + 1);
+  std::vector<unsigned char> pml(n + 2, 0), pml2(n + 2, 0);
+  auto fill_axis = [&](int axis, std::vector<c128>& is, std::vector<c128>& ah, std::vector<c64>& fis,
+                       std::vector<c64>& fah, std::vector<unsigned char>& pm) {
+    for (int k = 0; k <= n + 1; ++k) {
+      zc v = inv_stretch(sig_axis(axis, k * h), omega);
+      is[k] = to_c(v); fis[k] = to_f(v);
+    }
+    for (int k = 0; k <= n; ++k) {
+      zc v = stretch(sig_axis(axis, (k + 0.5) * h), omega) / (h * h);
+      ah[k] = to_c(v); fah[k] = to_f(v);
+    }
+    for (int k = 1; k <= n; ++k) {
+      bool t = sig_axis(axis, k * h) != 0.0 || sig_axis(axis, (k - 0.5) * h) != 0.0 ||
+               sig_axis(axis, (k + 0.5) * h) != 0.0;
+      pm[k] = t ? 1 : 0;
+    }
+  };
+  fill_axis(1, inv_s, a_half, f_inv_s, f_a_half, pml);
+  fill_axis(2, inv_s2, a_half2, f_inv_s2, f_a_half2, pml2);
   if ((st = dalloc(*p, &p->d_inv_s1, n + 2)) || (st = dalloc(*p, &p->d_a1, n + 1)) ||
       (st = dalloc(*p, &p->d_inv_s2, n + 2)) || (st = dalloc(*p, &p->d_a2, n + 1)) ||
       (st = dalloc(*p, &p->f_inv_s1, n + 2)) || (st = dalloc(*p, &p->f_a1, n + 1)) ||
@@ -355,15 +409,15 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
       (st = dalloc(*p, &p->d_pml1, n + 2)) || (st = dalloc(*p, &p->d_pml2, n + 2)))
     return fail(st);
   cudaMemcpy(p->d_inv_s1, inv_s.data(), (n + 2) * sizeof(c128), cudaMemcpyHostToDevice);
-  cudaMemcpy(p->d_inv_s2, inv_s.data(), (n + 2) * sizeof(c128), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_inv_s2, inv_s2.data(), (n + 2) * sizeof(c128), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_a1, a_half.data(), (n + 1) * sizeof(c128), cudaMemcpyHostToDevice);
-  cudaMemcpy(p->d_a2, a_half.data(), (n + 1) * sizeof(c128), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_a2, a_half2.data(), (n + 1) * sizeof(c128), cudaMemcpyHostToDevice);
   cudaMemcpy(p->f_inv_s1, f_inv_s.data(), (n + 2) * sizeof(c64), cudaMemcpyHostToDevice);
-  cudaMemcpy(p->f_inv_s2, f_inv_s.data(), (n + 2) * sizeof(c64), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->f_inv_s2, f_inv_s2.data(), (n + 2) * sizeof(c64), cudaMemcpyHostToDevice);
   cudaMemcpy(p->f_a1, f_a_half.data(), (n + 1) * sizeof(c64), cudaMemcpyHostToDevice);
-  cudaMemcpy(p->f_a2, f_a_half.data(), (n + 1) * sizeof(c64), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->f_a2, f_a_half2.data(), (n + 1) * sizeof(c64), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_pml1, pml.data(), n + 2, cudaMemcpyHostToDevice);
-  cudaMemcpy(p->d_pml2, pml.data(), n + 2, cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_pml2, pml2.data(), n + 2, cudaMemcpyHostToDevice);
   {   // the PML-free points form one index range [lo, hi) per axis (sigma vanishes away from the boundary)
     int lo = 0;
     while (lo < n && pml[lo + 1]) ++lo;
@@ -382,9 +436,11 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
       o[0] = (float)x;
       o[1] = (float)(x - (double)o[0]);
     };
-    std::vector<float> kis(4 * (n + 2)), ka(4 * (n + 1));
+    std::vector<float> kis(4 * (n + 2)), ka(4 * (n + 1)), kis2(4 * (n + 2)), ka2(4 * (n + 1));
     for (int k = 0; k <= n + 1; ++k) { split(inv_s[k].re, &kis[4 * k]); split(inv_s[k].im, &kis[4 * k + 2]); }
     for (int k = 0; k <= n; ++k) { split(a_half[k].re, &ka[4 * k]); split(a_half[k].im, &ka[4 * k + 2]); }
+    for (int k = 0; k <= n + 1; ++k) { split(inv_s2[k].re, &kis2[4 * k]); split(inv_s2[k].im, &kis2[4 * k + 2]); }
+    for (int k = 0; k <= n; ++k) { split(a_half2[k].re, &ka2[4 * k]); split(a_half2[k].im, &ka2[4 * k + 2]); }
     if ((st = dalloc(*p, &p->d_m0, N2)) || (st = dalloc(*p, &p->f_m0, N2)) || (st = dalloc(*p, &p->d_cinv2, N2)) ||
         (st = dalloc(*p, (float**)&p->k_m0, 2 * N2)) || (st = dalloc(*p, (float**)&p->k_inv_s1, 4 * (n + 2))) ||
         (st = dalloc(*p, (float**)&p->k_inv_s2, 4 * (n + 2))) || (st = dalloc(*p, (float**)&p->k_a1, 4 * (n + 1))) ||
@@ -396,9 +452,9 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
     hs::point_tables_kernel<<<(int)gb, 256>>>(p->d_m0, p->d_cinv2, p->f_m0, (float*)p->k_m0, (long long)N2, omega * omega);
     if (cudaStreamSynchronize(0) != cudaSuccess) return fail(HS_ECUDA);
     cudaMemcpy(p->k_inv_s1, kis.data(), kis.size() * sizeof(float), cudaMemcpyHostToDevice);
-    cudaMemcpy(p->k_inv_s2, kis.data(), kis.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->k_inv_s2, kis2.data(), kis2.size() * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(p->k_a1, ka.data(), ka.size() * sizeof(float), cudaMemcpyHostToDevice);
-    cudaMemcpy(p->k_a2, ka.data(), ka.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->k_a2, ka2.data(), ka2.size() * sizeof(float), cudaMemcpyHostToDevice);
   }
 
   // ---- per-block window x2 tables (moving profile of Eq. helma or the
@@ -409,11 +465,13 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
   for (auto& d : p->blocks) {
     d.s2_off = (int)s2win.size();
     // x2 absorption of the block's subproblem at coordinate x
+    // (the moving profiles start at the rows just outside the window: its
+    // Dirichlet rows wlo - 1 and whi + 1, b + k rows from the block)
     auto sig = [&](double x) {
-      if (d.kind == BK_F || d.kind == BK_E) return sigma_boundary(x, eta, C);
+      if (d.kind == BK_F || d.kind == BK_E || d.exact) return sig_axis(2, x);
       double s = 0.0;
-      if (d.kind == BK_LOWER || d.kind == BK_MIDDLE) s += sigma_moving(x - (d.lo - p->b) * h, eta_b, Cm);
-      if (d.kind == BK_UPPER || d.kind == BK_MIDDLE) s += sigma_moving((d.hi + p->b) * h - x, eta_b, Cm);
+      if (d.kind == BK_LOWER || d.kind == BK_MIDDLE) s += sigma_moving(x - (d.wlo - 1) * h, eta_b, Cm);
+      if (d.kind == BK_UPPER || d.kind == BK_MIDDLE) s += sigma_moving((d.whi + 1) * h - x, eta_b, Cm);
       return s;
     };
     for (int q = 0; q < d.w; ++q) s2win.push_back(to_c(inv_stretch(sig((d.wlo + q) * h), omega)));

@@ -31,3 +31,18 @@ def test_headline_stage_count():
     treat both fronts at once."""
     blocks = bench.blocks(2047, 12, 12, 12)
     assert len(blocks) == 173 and sum(u for _, u in blocks) == 2 * 172 + 1
+
+
+def test_sweep_bytes_count_the_band_factor():
+    """Algorithmic bytes of one application (complex64): every block's band
+    factor, w^2 + w entries per x1 column (L and D), once per solve, plus four
+    passes over the R right-hand sides."""
+    n, bp, b, dL, R = 511, 12, 12, 12, 4
+    lower, upper, mid = S.partition(n, bp, b, dL)
+    fac = 0
+    for blk in lower + upper:
+        w = blk.whi - blk.wlo + 1
+        fac += 2 * n * (w * w + w) * 8
+    w = mid.whi - mid.wlo + 1
+    fac += n * (w * w + w) * 8
+    assert bench.sweep_bytes(n, bp, b, dL, R) == fac + 4 * n * n * R * 8
