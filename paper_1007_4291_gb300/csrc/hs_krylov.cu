@@ -132,7 +132,23 @@ __global__ void __launch_bounds__(KT) dots_kernel(const typename AR::V* __restri
   typename AR::N nrm;
   AR::norm_zero(nrm);
   if (r < R) {
-    for (long long pt = (long long)blockIdx.x * 8 + warp; pt < npts; pt += (long long)gridDim.x * 8) {
+    // two points per iteration, so that the loads of both are in flight together
+    const long long stride = (long long)gridDim.x * 8;
+    long long pt = (long long)blockIdx.x * 8 + warp;
+    for (; pt + stride < npts; pt += 2 * stride) {
+      const long long e0 = pt * R + r, e1 = (pt + stride) * R + r;
+      const typename AR::V w0 = w[e0], w1 = w[e1];
+      typename AR::V v0[MAXJ], v1[MAXJ];
+#pragma unroll
+      for (int i = 0; i < MAXJ; ++i)
+        if (i < nv) { v0[i] = V[i * vstride + e0]; v1[i] = V[i * vstride + e1]; }
+      AR::norm_acc(nrm, w0);
+      AR::norm_acc(nrm, w1);
+#pragma unroll
+      for (int i = 0; i < MAXJ; ++i)
+        if (i < nv) { AR::acc_conj(acc[i], v0[i], w0); AR::acc_conj(acc[i], v1[i], w1); }
+    }
+    if (pt < npts) {
       const long long e = pt * R + r;
       const typename AR::V wv = w[e];
       AR::norm_acc(nrm, wv);
@@ -171,11 +187,15 @@ __global__ void reduce_parts_kernel(const c128* __restrict__ part, int nctas, in
   out[i * R + r] = s;
 }
 
-// w -= sum_i h[i][r] V_i ; part[cta][r] = partial |w_new|^2
+// w -= sum_i h[i][r] s[i][r] V_i (s = 1 when `iscale` is NULL: scaled
+// coefficients let the basis vectors stay unnormalised); also copied to
+// `wcopy` when given; part[cta][r] = partial |w_new|^2
 template <typename AR, int MAXJ>
 __global__ void __launch_bounds__(KT) update_kernel(const typename AR::V* __restrict__ V, long long vstride, int nv,
                                                     const c128* __restrict__ h, typename AR::V* __restrict__ w,
-                                                    long long npts, int R, c128* __restrict__ part) {
+                                                    long long npts, int R, c128* __restrict__ part,
+                                                    const double* __restrict__ iscale = nullptr,
+                                                    typename AR::V* __restrict__ wcopy = nullptr) {
   __shared__ double snrm[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = blockIdx.y * 32 + lane;
@@ -183,7 +203,11 @@ __global__ void __launch_bounds__(KT) update_kernel(const typename AR::V* __rest
   __syncthreads();
   typename AR::V hc[MAXJ];
 #pragma unroll
-  for (int i = 0; i < MAXJ; ++i) hc[i] = AR::coef((i < nv && r < R) ? h[i * R + r] : c128{0, 0});
+  for (int i = 0; i < MAXJ; ++i) {
+    c128 hv = (i < nv && r < R) ? h[i * R + r] : c128{0, 0};
+    if (iscale && i < nv && r < R) hv = cscale(hv, iscale[i * R + r]);
+    hc[i] = AR::coef(hv);
+  }
   typename AR::N nrm;
   AR::norm_zero(nrm);
   if (r < R) {
@@ -194,6 +218,7 @@ __global__ void __launch_bounds__(KT) update_kernel(const typename AR::V* __rest
       for (int i = 0; i < MAXJ; ++i)
         if (i < nv) AR::sub_prod(wv, hc[i], V[i * vstride + e]);
       w[e] = wv;
+      if (wcopy) wcopy[e] = wv;
       AR::norm_acc(nrm, wv);
     }
   }
@@ -544,12 +569,12 @@ struct Solver {
     reduce_parts_kernel<<<((nv + 1) * R + 255) / 256, 256, 0, s>>>(w.part, nctas, mj + 1, nv + 1, R, w.h);
   }
   // v -= V h ; |v|^2 -> w.h row `slot`
-  void update(const V* Vb, int nv, V* v, int slot) {
+  void update(const V* Vb, int nv, V* v, int slot, const double* iscale = nullptr, V* vcopy = nullptr) {
     const dim3 g = grid();
     note_launch();
-    if (nv <= 8) update_kernel<AR, 8><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part);
-    else if (nv <= 16) update_kernel<AR, 16><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part);
-    else update_kernel<AR, 32><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part);
+    if (nv <= 8) update_kernel<AR, 8><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part, iscale, vcopy);
+    else if (nv <= 16) update_kernel<AR, 16><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part, iscale, vcopy);
+    else update_kernel<AR, 32><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part, iscale, vcopy);
     note_launch();
     reduce_parts_kernel<<<(R + 255) / 256, 256, 0, s>>>(w.part, nctas, 1, 1, R, w.h + (long long)slot * R);
   }
@@ -867,7 +892,8 @@ int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxi
   const size_t nct = (size_t)sm_count() * 2;
   const size_t b1 = al256((m + 1) * vs * sizeof(c64)), b2 = al256(m * vs * sizeof(c64)), b3 = al256(vs * sizeof(cdf));
   const size_t b4 = al256(nct * 33 * R * sizeof(c128)), b5 = al256(34 * R * sizeof(c128)), b6 = al256(R * 16);
-  const size_t need = b1 + b2 + 3 * b3 + b4 + b5 + b6;
+  const size_t b7 = al256((size_t)(m + 1) * R * sizeof(double));
+  const size_t need = b1 + b2 + 3 * b3 + b4 + b5 + b6 + b7;
   if (kp.bytes < need) {
     if (kp.base) cudaFree(kp.base);
     kp.base = nullptr;
@@ -884,7 +910,8 @@ int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxi
   cdf* rb = (cdf*)q; q += b3;
   w.part = (c128*)q; q += b4;
   w.h = (c128*)q; q += b5;
-  w.s = q;
+  w.s = q; q += b6;
+  double* d_inu2 = (double*)q;     // 1 / |V_i|^2 per basis vector and RHS
   Solver<DF64> K{p, R, (long long)npts, (long long)vs, s, w, sm_count() * 2, {}};
   Solver<F32> B{p, R, (long long)npts, (long long)vs, s, w, sm_count() * 2, {}};
   c64* Vb = (c64*)w.V;
@@ -910,6 +937,11 @@ int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxi
   std::vector<double> cs((size_t)R * m), relres(R, 1.0), scl(R);
   std::vector<float> sclf(R);
   std::vector<char> active(R);
+  // The basis vectors V_i are kept unnormalised: v_i = V_i / nu_i.  The
+  // update divides its coefficients by nu_i^2 and writes the next sweep input
+  // in the same pass, and the Hessenberg entries and the final combination
+  // take the norms on the host, so no pass rescales the vectors.
+  std::vector<double> nu((size_t)(m + 1) * R, 0.0), inu2((size_t)(m + 1) * R, 0.0);
   int it = 0, cycles = 0, applies = 0, st = HS_OK;
   void* const u_saved = p.d_u;
   while (true) {
@@ -933,6 +965,11 @@ int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxi
     cudaMemcpyAsync(w.s, sclf.data(), R * sizeof(float), cudaMemcpyHostToDevice, s);
     note_launch();
     df_to_c64_scaled_kernel<<<sm_count() * 8, 256, 0, s>>>(rb, (const float*)w.s, Vb, vs, R, Z);   // v_0, z_0 input
+    for (int r = 0; r < R; ++r) {          // V_0 = r / |r| (zero for converged RHS)
+      nu[r] = active[r] ? 1.0 : 0.0;
+      inu2[r] = nu[r];
+    }
+    cudaMemcpyAsync(d_inu2, inu2.data(), R * sizeof(double), cudaMemcpyHostToDevice, s);
     int k = 0;
     for (int j = 0; j < m; ++j) {
       c64* W1 = Vb + (long long)(j + 1) * vs;
@@ -947,22 +984,29 @@ int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxi
       st = matvec_internal_f32(p, Zj, W1, R, s);   // A z_j in FP32 (the cycle's precision)
       if (st != HS_OK) break;
       cudaEventRecord(ev[2], s);
-      B.dots(Vb, j + 1, W1);                   // FP32 classical Gram-Schmidt
-      B.update(Vb, j + 1, W1, 32);
+      // FP32 classical Gram-Schmidt on the unnormalised basis: d_i = V_i^H W,
+      // W -= sum_i (d_i / nu_i^2) V_i, written also as the next sweep's input
+      B.dots(Vb, j + 1, W1);
+      B.update(Vb, j + 1, W1, 32, d_inu2, j + 1 < m ? Zj + vs : nullptr);
       fetch_h(33);
-      std::vector<c128> h1(hbuf.begin(), hbuf.begin() + (size_t)(j + 1) * R);
-      std::vector<double> nw(R), inv(R);
+      // W = A M V_j = nu_j A z_j: the normalised entries are d_i / (nu_i nu_j),
+      // and |W'| = nu_j |w'|, so nu_{j+1} = |W'| and h_{j+1,j} = nu_{j+1} / nu_j
+      std::vector<c128> h1((size_t)(j + 1) * R);
+      std::vector<double> nw(R);
+      double* nu_j = &nu[(size_t)j * R];
+      double* nu_n = &nu[(size_t)(j + 1) * R];
       for (int r = 0; r < R; ++r) {
-        nw[r] = std::sqrt(hbuf[32 * R + r].re);
-        inv[r] = (active[r] && nw[r] > 0) ? 1.0 / nw[r] : 0.0;
+        nu_n[r] = std::sqrt(hbuf[32 * R + r].re);
+        inu2[(size_t)(j + 1) * R + r] = nu_n[r] > 0 ? 1.0 / (nu_n[r] * nu_n[r]) : 0.0;
+        nw[r] = nu_j[r] > 0 ? nu_n[r] / nu_j[r] : 0.0;
+        for (int i = 0; i <= j; ++i) {
+          const double den = nu[(size_t)i * R + r] * nu_j[r];
+          const c128 d = hbuf[(size_t)i * R + r];
+          h1[(size_t)i * R + r] = den > 0 ? c128{d.re / den, d.im / den} : c128{0, 0};
+        }
       }
-      {                                           // v_{j+1}, and the next sweep's input
-        for (int r = 0; r < R; ++r) sclf[r] = (float)inv[r];
-        cudaMemcpyAsync(w.s, sclf.data(), R * sizeof(float), cudaMemcpyHostToDevice, s);
-        note_launch();
-        scale_f32_kernel<<<sm_count() * 8, 256, 0, s>>>(W1, (const float*)w.s, W1, vs, R,
-                                                        j + 1 < m ? Zj + vs : nullptr);
-      }
+      cudaMemcpyAsync(d_inu2 + (size_t)(j + 1) * R, &inu2[(size_t)(j + 1) * R], R * sizeof(double),
+                      cudaMemcpyHostToDevice, s);
       cudaEventRecord(ev[3], s);
       cudaEventSynchronize(ev[3]);
       t_apply += elapsed(ev[0], ev[1]);
@@ -1003,7 +1047,12 @@ int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxi
         for (int q2 = i + 1; q2 < k; ++q2) acc -= Hr[i * m + q2] * yr[q2];
         yr[i] = (active[r] && Hr[i * m + i] != 0.0) ? acc / Hr[i * m + i] : 0.0;
       }
-      for (int i = 0; i < k; ++i) y[(size_t)i * R + r] = c128{yr[i].real(), yr[i].imag()};
+      // x += sum_i y_i z_i, z_i = Z_i / nu_i
+      for (int i = 0; i < k; ++i) {
+        const double ni = nu[(size_t)i * R + r];
+        const zc yi = ni > 0 ? yr[i] / ni : zc(0.0);
+        y[(size_t)i * R + r] = c128{yi.real(), yi.imag()};
+      }
     }
     cudaMemcpyAsync(w.h, y.data(), y.size() * sizeof(c128), cudaMemcpyHostToDevice, s);
     {

@@ -251,14 +251,6 @@ __global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase1_kernel(SweepA
   __syncthreads();
   if (tid >= NCONS) {
     if (tid == NCONS) {
-#ifndef HS_NO_PREFETCH
-      // the separator system's factors of this chunk's right separator go to
-      // L2 now: the separator solve that follows this kernel reads them in a
-      // serial chain, one block per step, and would otherwise wait for DRAM
-      if (a.P > 1 && k < a.P - 1)
-        prefetch_l2(reinterpret_cast<const C*>(a.red) + d.red_off + (long long)k * red_elems(W),
-                    (uint32_t)(red_elems(W) * sizeof(C)));
-#endif
       ring_producer(full, empty, S13, ncol, a.spin, a.status, front, [&](int t) {
         mbar_arrive_expect_tx(&full[t % S13], pbytes);
         tma_bulk_g2s(const_cast<C*>(stage(t)), fac + (long long)(l + t) * pe, pbytes, &full[t % S13]);
@@ -733,270 +725,6 @@ __global__ void __launch_bounds__(2 * npart<R>() * wpc_max<R>() * 32 + 64) phase
   if (!ok && lane == 0) set_status(a.status, HS_ETIMEOUT, front, -2);
 }
 
-// Separator solve for complex64 factors with one warp per half chain.  The
-// chain steps are W x W products whose latency, not their arithmetic, sets
-// the pace: each warp spreads a product over all 32 lanes (lane = 4 g + cq
-// owns rows g + 8 i, i < NI, and the column quarter cq NC .. cq NC + NC - 1),
-// forms its partial sums and adds the four quarters with two xor shuffles,
-// so that a step is one shared-memory load of the chain vector, NC
-// multiply-adds and the shuffles, with no exchange between warps.  The four
-// lanes of a row group end with the same bits; the lane with cq = i stores
-// row g + 8 i.  Same recurrences, ring order and wait agreements as
-// phase2_kernel (see there); the two warps of a right-hand side meet twice
-// on a named barrier (psi'_{m+1}, then x_m).
-template <int W> struct SepLanes {
-  static constexpr int NI = (W + 7) / 8;   // rows per lane
-  static constexpr int NC = W / 4;         // columns per lane
-};
-
-__device__ __forceinline__ float shfl_xor_f(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
-
-template <int W>
-__global__ void __launch_bounds__(2 * WPC_MAX * 32 + 64) phase2w_kernel(SweepArgs a) {
-  using C = cplx<float>;
-  constexpr int LDP = W + 2;
-  constexpr int S2 = Ring2<float, W>::S;
-  constexpr int NI = SepLanes<W>::NI, NC = SepLanes<W>::NC;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);     // [2][S2]
-  uint64_t* empty = full + 2 * S2;                            // [2][S2]
-  const int front = blockIdx.z;
-  const BlockDesc& d = a.blk[front];
-  const long long re = red_elems(W);
-  const uint32_t rbytes = (uint32_t)(re * sizeof(C));
-  const size_t sstride = round128(rbytes);
-  const int K = a.P - 1, m = twist_index(K), nb = K - 1 - m;
-  const int nuse0 = 2 * m + 1, nuse1 = nb > 0 ? 2 * nb + 1 : 0;
-  C* rz = reinterpret_cast<C*>(smem_raw + 256 + (size_t)2 * S2 * sstride);
-  const C* red = reinterpret_cast<const C*>(a.red) + d.red_off;
-  const int tid = threadIdx.x;
-  const int wpc = ((int)blockDim.x - 64) / 64;   // RHS per CTA: two chain warps each
-  auto stage = [&](int h, int u) { return reinterpret_cast<C*>(smem_raw + 256 + (size_t)(h * S2 + u % S2) * sstride); };
-  auto slot_of = [&](int h, int u) {
-    if (h == 0) return u <= m ? u : 2 * m - u;              // 0..m-1, m, m-1..0
-    return u < nb ? K - 1 - u : m + (u - nb);               // K-1..m+1, m..K-1
-  };
-  if (tid == 0) {
-    for (int u = 0; u < 2 * S2; ++u) {
-      mbar_init(&full[u], 1);
-      mbar_init(&empty[u], wpc);    // every RHS's warp of the half releases each use
-    }
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (tid >= 2 * wpc * 32) {
-    const int h = (tid - 2 * wpc * 32) >> 5;
-    const int nu = h == 0 ? nuse0 : nuse1;
-    if ((tid & 31) == 0 && nu > 0)
-      ring_producer(full + h * S2, empty + h * S2, S2, nu, a.spin, a.status, front, [&](int t) {
-        mbar_arrive_expect_tx(&full[h * S2 + t % S2], rbytes);
-        tma_bulk_g2s(stage(h, t), red + (long long)slot_of(h, t) * re, rbytes, &full[h * S2 + t % S2]);
-      });
-    return;
-  }
-  const int lane = tid & 31, wq = tid >> 5;
-  const int rhs = wq % wpc, half = wq / wpc;
-  const int g = lane >> 2, cq = lane & 3, c0 = cq * NC;
-  const int r = blockIdx.y * wpc + rhs;
-  const bool valid = r < a.R;
-  const int rr = valid ? r : (a.R - 1);
-  const int pl = lane < W ? lane : 0;
-  const int pair_id = 1 + rhs;
-  const C* rcb = reinterpret_cast<const C*>(a.rc);
-  const C* lcb = reinterpret_cast<const C*>(a.lc);
-  C* xsb = reinterpret_cast<C*>(a.xs);
-  const long long fb = (long long)front * a.P;
-  // per RHS: [0..K-1] rho, overwritten by psi; then x buffers of the top
-  // half [2][W], of the bottom half [2][W], the twist vector [W], x_m [W]
-  C* myrz = rz + (size_t)rhs * ((K + 3) * W + 8 * W);
-  C* xbt = myrz + (size_t)K * W;
-  C* xbb = xbt + 2 * W;
-  C* tv = xbb + 2 * W;
-  C* xm = tv + W;
-  uint64_t* fl = full + half * S2;
-  uint64_t* em = empty + half * S2;
-  int row[NI];
-  bool rv[NI];
-#pragma unroll
-  for (int i = 0; i < NI; ++i) {
-    row[i] = g + 8 * i;
-    rv[i] = row[i] < W;
-  }
-  // rho_k of this half's separators (top: 0..m, bottom: m+1..K-1)
-  const int k_lo = half == 0 ? 0 : m + 1, k_hi = half == 0 ? m + 1 : K;
-  for (int k0 = k_lo; k0 < k_hi; k0 += 16) {
-    C v1[16], v2[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int k = min(k0 + q, k_hi - 1);
-      v1[q] = rcb[((fb + k) * a.R + rr) * W + pl];
-      v2[q] = lcb[((fb + k + 1) * a.R + rr) * W + pl];
-    }
-#pragma unroll
-    for (int q = 0; q < 16; ++q)
-      if (k0 + q < k_hi && lane < W) myrz[(k0 + q) * W + lane] = C{-(v1[q].re + v2[q].re), -(v1[q].im + v2[q].im)};
-  }
-  __syncwarp();
-  // acc[i] += sum over this lane's columns of M[row i][c] v[c] (M row-major, stride LDP)
-  auto rows_dot = [&](C (&acc)[NI], const C* M, const C* v) {
-    C vv[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) vv[c] = v[c0 + c];
-#pragma unroll
-    for (int i = 0; i < NI; ++i) {
-      if (!rv[i]) continue;
-      const C* mr = M + row[i] * LDP + c0;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) cfma(acc[i], mr[c], vv[c]);
-    }
-  };
-  // the transposed operand for the next backward step: ft[i][c] = M[c0 + c][row i]
-  auto load_t = [&](C (&ft)[NI][NC], const C* M) {
-#pragma unroll
-    for (int i = 0; i < NI; ++i)
-#pragma unroll
-      for (int c = 0; c < NC; ++c) ft[i][c] = rv[i] ? M[(c0 + c) * LDP + row[i]] : C{0, 0};
-  };
-  auto ft_dot = [&](C (&acc)[NI], const C (&ft)[NI][NC], const C* v) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const C x = v[c0 + c];
-#pragma unroll
-      for (int i = 0; i < NI; ++i) cfms(acc[i], ft[i][c], x);
-    }
-  };
-  auto quad_sum = [&](C (&acc)[NI]) {
-#pragma unroll
-    for (int i = 0; i < NI; ++i) {
-      acc[i].re += shfl_xor_f(acc[i].re, 1);
-      acc[i].im += shfl_xor_f(acc[i].im, 1);
-      acc[i].re += shfl_xor_f(acc[i].re, 2);
-      acc[i].im += shfl_xor_f(acc[i].im, 2);
-    }
-  };
-  // the lane with cq = i stores row i of its group
-  auto put = [&](C* dst, const C (&v)[NI]) {
-#pragma unroll
-    for (int i = 0; i < NI; ++i)
-      if (cq == i && rv[i]) dst[row[i]] = v[i];
-  };
-  auto put_x = [&](int k, const C (&v)[NI]) {
-    if (!valid) return;
-#pragma unroll
-    for (int i = 0; i < NI; ++i)
-      if (cq == i && rv[i]) xsb[((fb + k) * a.R + r) * W + row[i]] = v[i];
-  };
-  auto zero = [&](C (&acc)[NI]) {
-#pragma unroll
-    for (int i = 0; i < NI; ++i) acc[i] = C{0, 0};
-  };
-  auto waitp = [&](int u) { return __all_sync(0xffffffffu, mbar_wait_bounded(&fl[u % S2], (u / S2) & 1, a.spin)); };
-  auto release = [&](int u) {
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&em[u % S2]);
-  };
-  bool ok = true;
-  int t = 0;
-  // ---- forward half chains: psi_k = rho_k - F_k psi_{k-1} (top),
-  //      psi'_k = rho_k - F'_k psi'_{k+1} (bottom)
-  {
-    const int nsteps = half == 0 ? m : nb;
-    for (int u = 0; u < nsteps; ++u, ++t) {
-      const int k = half == 0 ? u : K - 1 - u;
-      const bool first = u == 0;
-      if (!waitp(t)) { ok = false; break; }
-      if (!first) {
-        C rho[NI], acc[NI];
-#pragma unroll
-        for (int i = 0; i < NI; ++i) rho[i] = rv[i] ? myrz[k * W + row[i]] : C{0, 0};
-        zero(acc);
-        rows_dot(acc, stage(half, t) + W * LDP, myrz + (half == 0 ? k - 1 : k + 1) * W);
-        quad_sum(acc);
-#pragma unroll
-        for (int i = 0; i < NI; ++i) acc[i] = csub(rho[i], acc[i]);
-        __syncwarp();
-        put(myrz + k * W, acc);
-      }
-      release(t);
-    }
-  }
-  ok = named_barrier_and(pair_id, 64, ok);
-  C ft[NI][NC];
-  // ---- twist (top half): x_m = Gamma_m (rho_m - F_m psi_{m-1} - F'_m psi'_{m+1})
-  if (half == 0 && ok) {
-    if (!waitp(t)) {
-      ok = false;
-    } else {
-      const C* Gm = stage(0, t);
-      C acc[NI], v[NI];
-      zero(acc);
-      if (m >= 1) rows_dot(acc, Gm + W * LDP, myrz + (m - 1) * W);
-      if (m < K - 1) rows_dot(acc, Gm + 2 * W * LDP, myrz + (m + 1) * W);
-      quad_sum(acc);
-#pragma unroll
-      for (int i = 0; i < NI; ++i) v[i] = csub(rv[i] ? myrz[m * W + row[i]] : C{0, 0}, acc[i]);
-      put(tv, v);
-      __syncwarp();
-      zero(acc);
-      rows_dot(acc, Gm, tv);
-      quad_sum(acc);
-      if (m >= 1) load_t(ft, Gm + W * LDP);      // F_m for x_{m-1}
-      put(xm, acc);
-      put(xbt, acc);
-      put_x(m, acc);
-      release(t);
-      ++t;
-    }
-  }
-  ok = named_barrier_and(pair_id, 64, ok);
-  // ---- backward half chains
-  if (half == 0 && ok) {
-    // x_k = Gamma_k psi_k - F_{k+1}^t x_{k+1}, k = m-1 .. 0
-    int cur = 0;
-    for (int k = m - 1; k >= 0; --k, ++t) {
-      if (!waitp(t)) { ok = false; break; }
-      const C* Gk = stage(0, t);
-      C acc[NI];
-      zero(acc);
-      rows_dot(acc, Gk, myrz + k * W);
-      ft_dot(acc, ft, xbt + cur * W);
-      quad_sum(acc);
-      if (k >= 1) load_t(ft, Gk + W * LDP);
-      put(xbt + (cur ^ 1) * W, acc);
-      put_x(k, acc);
-      cur ^= 1;
-      release(t);
-    }
-  } else if (half == 1 && ok && nb > 0) {
-    // F'_m from the twist slot, then x_k = Gamma'_k psi'_k - F'_{k-1}^t x_{k-1}, k = m+1 .. K-1
-    if (!waitp(t)) {
-      ok = false;
-    } else {
-      load_t(ft, stage(1, t) + 2 * W * LDP);
-      release(t);
-      ++t;
-      const C* xprev = xm;
-      int cur = 0;
-      for (int k = m + 1; k < K; ++k, ++t) {
-        if (!waitp(t)) { ok = false; break; }
-        const C* Gk = stage(1, t);
-        C acc[NI];
-        zero(acc);
-        rows_dot(acc, Gk, myrz + k * W);
-        ft_dot(acc, ft, xprev);
-        quad_sum(acc);
-        if (k < K - 1) load_t(ft, Gk + W * LDP);
-        put(xbb + cur * W, acc);
-        put_x(k, acc);
-        xprev = xbb + cur * W;
-        cur ^= 1;
-        release(t);
-      }
-    }
-  }
-  if (!ok && lane == 0) set_status(a.status, HS_ETIMEOUT, front, -2);
-}
-
 // ---------------------------------------------------------------- phase 3
 // Back substitution over the chunk's interior columns from the right
 // separator: x_j = z_j - G_j (C_j x_{j+1}); output rows get the left-spike
@@ -1200,8 +928,6 @@ void set_attrs_w() {
     cudaFuncSetAttribute(phase1_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(phase3_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(phase2_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    if constexpr (sizeof(R) == 4)
-      cudaFuncSetAttribute(phase2w_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   });
 }
 
@@ -1226,12 +952,7 @@ int run_stage_w(const Plan& p, SweepArgs a, cudaStream_t s) {
   if (a.P > 1) {
     dim3 g2(1, (a.R + wpc - 1) / wpc, a.nfront);
     note_launch();
-#ifndef HS_OLD_P2
-    if constexpr (sizeof(R) == 4)
-      phase2w_kernel<W><<<g2, 2 * wpc * 32 + 64, phase2_smem<R, W>(a.P - 1, wpc), s>>>(a);
-    else
-#endif
-      phase2_kernel<R, W><<<g2, 2 * npart<R>() * wpc * 32 + 64, phase2_smem<R, W>(a.P - 1, wpc), s>>>(a);
+    phase2_kernel<R, W><<<g2, 2 * npart<R>() * wpc * 32 + 64, phase2_smem<R, W>(a.P - 1, wpc), s>>>(a);
   }
   note_launch();
   phase3_kernel<R, W><<<g13, TL::NCONS + 32, sm3, s>>>(a);

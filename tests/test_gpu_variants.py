@@ -61,7 +61,7 @@ SINGLE_CASES = [
     (64, 6, 5, 5, 8, 2),      # even n, remainder block at the top, b < bp
     (71, 6, 6, 12, 8, 4),     # ragged last chunk, d = 12
     (47, 5, 5, 3, 47, 2),     # a single chunk
-    (40, 6, 6, 40, 16, 1),    # the whole grid above F is one top block
+    (24, 6, 6, 18, 16, 1),    # the whole grid above F is one top block (window of 23 rows)
 ]
 
 
