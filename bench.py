@@ -394,7 +394,10 @@ def batched_uneven(stream, nprob=32, nrhs=8, big_n=2047, big_nrhs=256):
 def three_d(stream, n=63, nrhs=16):
     """3D: n = 63, omega/2pi = 4, PML 6, moving PML 5, d = 1, alpha = 1,
     smooth random velocity, 16 point sources; time-to-1e-6 per frontal-GEMM
-    precision (3xTF32 and one-pass TF32 tensor cores, FP32 FMA, FP64)."""
+    precision (3xTF32, one-pass TF32, 3xBF16 and one-pass BF16 tensor cores,
+    FP32 FMA, FP64).  Each line carries the setup's arithmetic (frontal GEMM
+    and pivot-block inversion flops, hs_setup_flops) and its rate over the
+    whole setup time, a lower bound on the frontal kernels' own rate."""
     import torch
     from paper_1007_4291_gb300 import hs
     from paper_1007_4291_gb300 import inputs as I
@@ -403,6 +406,7 @@ def three_d(stream, n=63, nrhs=16):
     omega = 2 * np.pi * 4.0
     out = {"n": n, "nrhs": nrhs, "omega_over_2pi": 4.0}
     for name, prec, mode in (("c64_3xtf32_tensor", hs.HS_C64, 3), ("c64_tf32_tensor", hs.HS_C64, 1),
+                             ("c64_3xbf16_tensor", hs.HS_C64, 4), ("c64_bf16_tensor", hs.HS_C64, 2),
                              ("c64_fp32_fma", hs.HS_C64, 0), ("c128_fp64", hs.HS_C128, 0)):
         opt = hs.hs_default_options(alpha=1.0, pml_C=20.0, layers_per_step=1, factor_prec=prec, max_nrhs=nrhs,
                                     frontal_gemm=mode)
@@ -413,6 +417,7 @@ def three_d(stream, n=63, nrhs=16):
             plan = hs.hs_setup(c, omega, n, 3, 6, 5, opt, stream)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
+            gfl, ifl = hs.hs_setup_flops(plan)
             u = torch.zeros_like(f)
             code, info = hs.hs_solve(plan, f, u, nrhs, 1e-6, 200, stream)
             torch.cuda.synchronize()
@@ -420,7 +425,9 @@ def three_d(stream, n=63, nrhs=16):
             hs.hs_destroy(plan)
             best = {"status": code, "time_to_1e6_s": t2 - t0, "setup_s": t1 - t0, "solve_s": t2 - t1,
                     "iterations": info["iterations"], "max_relres": info["max_relres"],
-                    "ms_per_apply": info["t_apply_ms"] / max(info["applies"], 1)}
+                    "ms_per_apply": info["t_apply_ms"] / max(info["applies"], 1),
+                    "setup_gemm_flops": gfl, "setup_inverse_flops": ifl,
+                    "setup_tflops_over_whole_setup": (gfl + ifl) / (t1 - t0) / 1e12}
         out[name] = best
     return out
 
@@ -532,6 +539,50 @@ def solve_variant(stream, wl, args, label, **kw):
                "t_apply_ms": info["t_apply_ms"], "t_orth_ms": info["t_orth_ms"]}
     del f, u
     torch.cuda.empty_cache()
+    hs.hs_release_workspace()
+    return out
+
+
+def paper_workloads(stream, ns=(1023, 2047), tol=1e-3):
+    """The paper's Sec. 3 grid on the GPU: q = 8 points per wavelength
+    (omega/2pi = (n+1)/8), alpha = 2, b = d = 12, two fronts; velocity fields
+    lens / vertical waveguide / random (synthetic stand-ins for the paper's
+    figures), forces Test 1 (point source at (0.5, 0.125)) and Test 2 (wave
+    packet from (0.125, 0.125) along (1, 1)); one RHS each, FGMRES to `tol` in
+    the true residual.  The paper's counts (left GMRES on M A, preconditioned
+    residual, its own fields; context only) are listed beside."""
+    import torch
+    from paper_1007_4291_gb300 import hs
+    from paper_1007_4291_gb300 import inputs as I
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_2d_iterations.json")))
+    paper = {(t["table"], r["n"], r["test"]): r["n_iter"] for t in gold["tables"] for r in t["rows"] if r["q"] == 8}
+    tables = {"lens": "2DPML1", "waveguide": "2DPML2", "random": "2DPML3"}
+    out = {"what": "FGMRES to %g (true residual), 1 RHS, q = 8, b = d = 12, alpha = 2" % tol, "runs": []}
+    for n in ns:
+        omega = 2 * np.pi * (n + 1) / 8.0
+        fields = {"lens": I.lens_velocity(n), "waveguide": I.waveguide_velocity(n), "random": I.random_velocity(n, 0)}
+        forces = {1: I.centered_source(n, center=(0.5, 0.125)), 2: I.wave_packet(n, omega)}
+        for vname, c in fields.items():
+            opt = hs.hs_default_options(alpha=2.0, pml_C=20.0, layers_per_step=12, max_nrhs=1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan = hs.hs_setup(np.ascontiguousarray(c.ravel()), omega, n, 2, 12, 12, opt, stream)
+            torch.cuda.synchronize()
+            t_setup = time.perf_counter() - t0
+            try:
+                for test, f in forces.items():
+                    fg = torch.from_numpy(f).to("cuda")
+                    ug = torch.zeros_like(fg)
+                    torch.cuda.synchronize()
+                    t1 = time.perf_counter()
+                    code, info = hs.hs_solve(plan, fg, ug, 1, tol, 200, stream)
+                    torch.cuda.synchronize()
+                    out["runs"].append({"n": n, "omega_over_2pi": (n + 1) / 8.0, "velocity": vname, "test": test,
+                                        "status": code, "iterations": info["iterations"],
+                                        "paper_iterations": paper.get((tables[vname], n, test)),
+                                        "setup_s": t_setup, "solve_s": time.perf_counter() - t1})
+            finally:
+                hs.hs_destroy(plan)
     hs.hs_release_workspace()
     return out
 
@@ -697,6 +748,7 @@ def run_ours(args):
             stream, wl, args, "tuning outside the paper: moving PMLs at twice the boundary C (Eq. helma reuses C), "
             "same workload and tolerance", moving_pml_C=2.0 * wl["C"])
         line["comparator_fp64"] = comparator_fp64(args, wl, stream)
+        line["paper_workloads"] = paper_workloads(stream)
         line["batched_uneven"] = batched_uneven(stream)
         line["three_d"] = three_d(stream)
     if rank == 0 and world == 1 and not args.no_cpu:

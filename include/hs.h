@@ -76,9 +76,11 @@ typedef struct {
                             hs_attach_cnn uses mode 0).                                      default 1 */
   double inner_tol;      /* refinement cycles end when their residual estimate has fallen by this
                             factor (or below tol).                                             default 1e-4 */
-  int frontal_gemm;      /* 3D setup, frontal Schur updates of complex64 factors: 0 CUDA-core FP32
-                            FMA, 1 TF32 tensor cores (one pass), 3 3xTF32 tensor cores (split
-                            operands, FP32-level accuracy).  Complex128 factors use FP64 FMA.   default 3 */
+  int frontal_gemm;      /* 3D setup, frontal Schur updates of complex64 factors (Sec. 4.2): 0 CUDA-
+                            core FP32 FMA; tensor cores with FP32 accumulation: 1 TF32 (one pass),
+                            3 3xTF32 (split operands, FP32-level accuracy), 2 BF16 (one pass),
+                            4 3xBF16 (split operands, about 16 significant bits).  Complex128
+                            factors use FP64 FMA.                                             default 3 */
   const char* tune_cache;/* path of the table written by hs_autotune; with chunk = 0, hs_setup
                             takes the chunk length (and, with sep_rhs_per_cta = 0, the separator
                             grouping) from it when it holds the problem's key.  NULL: not used.
@@ -324,6 +326,13 @@ int hs_sync(hs_plan* plan, void* stream);
 
 /* Status recorded by device kernels since setup (HS_OK if none). */
 int hs_last_device_status(hs_plan* plan);
+
+/* Arithmetic of a 3D plan's setup (Sec. 4.2, Algorithm 5), for rooflines:
+ * real flops of the frontal Schur-update GEMMs (L = F21 G, F22 -= L F12;
+ * 8 per complex multiply-add) and of the front pivot-block inversions
+ * (8 S^3 for an S x S block).  HOST outputs (either may be NULL); 0 for 2D
+ * plans. */
+int hs_setup_flops(const hs_plan* plan, double* gemm_flops, double* inverse_flops);
 
 /* Bytes of device memory owned by the plan (factors, tables, sweep workspace). */
 long long hs_plan_bytes(const hs_plan* plan);

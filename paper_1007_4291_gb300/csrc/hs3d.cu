@@ -653,13 +653,16 @@ int setup3_t(Plan& p, Plan3& q, cudaStream_t s) {
       j1.push_back(GemmJob{f + (long long)it.S * LD, f, Lm, LD, LD, it.S, it.Bd, it.S, it.S, 1, 0});
       j2.push_back(GemmJob{Lm, f + it.S, f + (long long)it.S * LD + it.S, it.S, LD, LD, it.Bd, it.Bd, it.S, -1, 1});
     }
+    for (auto& it : its) q.inv_flops += 8.0 * it.S * (double)it.S * it.S;
+    for (auto* jobs : {&j1, &j2})
+      for (auto& g : *jobs) q.gemm_flops += 8.0 * g.M * (double)g.N * g.K;
     const bool tc = sizeof(R) == 4 && p.opt.frontal_gemm != 0;
     for (auto* jobs : {&j1, &j2}) {
       if (jobs->empty()) continue;
       if (tc) {
         std::vector<TcGemmJob> tj;
         for (auto& g : *jobs) tj.push_back(TcGemmJob{g.A, g.B, g.C, g.lda, g.ldb, g.ldc, g.M, g.N, g.K, (float)g.alpha, g.beta});
-        const int s2 = zgemm_tf32_batched(tj, p.opt.frontal_gemm == 3 ? 1 : 0, p.d_status, p.opt.spin_budget, s);
+        const int s2 = zgemm_tc_batched(tj, p.opt.frontal_gemm, p.d_status, p.opt.spin_budget, s);
         if (s2 != HS_OK) { st = s2; break; }
         continue;
       }

@@ -40,6 +40,8 @@ struct Plan3 {
   void* d_jobs = nullptr;
   std::vector<StageLists> stage_lists;
   StageLists middle_lists;
+  double gemm_flops = 0;     // real flops of the frontal Schur-update GEMMs of the setup (8 per complex MAC)
+  double inv_flops = 0;      // real flops of the front pivot-block inversions (8 S^3 each)
 };
 
 int prepare_plan3(Plan& p);                 // tree, window tables, solve workspace

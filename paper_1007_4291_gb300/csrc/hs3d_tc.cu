@@ -6,8 +6,10 @@
 // real M x 2K matrix of its interleaved (re, im) storage and
 //   Bt[2n + c][2k + d] = { Br, -Bi ; Bi, Br }[c][d]   (rows = output columns),
 // the interleaved complex result is A Bt^t.  Precision modes: one TF32 pass
-// (operands truncated to 10-bit mantissas), or the 3xTF32 split a = a_hi +
-// a_lo with a_hi b_hi + a_hi b_lo + a_lo b_hi, which restores FP32 accuracy.
+// (operands truncated to 10-bit mantissas), the 3xTF32 split a = a_hi + a_lo
+// with a_hi b_hi + a_hi b_lo + a_lo b_hi, which restores FP32 accuracy, and
+// the same two with BF16 operands (8-bit mantissas, rounded to nearest; the
+// split keeps about 16 bits).
 //
 // A CTA computes a 128 x 32 complex tile (MMA M = 128, N = 64 real columns)
 // and loops over K in chunks of 16 complex (32 real) values: its threads
@@ -17,6 +19,7 @@
 // (bounded) before the chunk's buffers are reused.  The epilogue reads the
 // accumulator rows of each warp's TMEM lane quarter.
 #include <algorithm>
+#include <cuda_bf16.h>
 #include "hs_internal.cuh"
 #include "hs_device.cuh"
 #include "hs_tc.cuh"
@@ -34,27 +37,61 @@ constexpr int KR = 2 * KC;     // real K per chunk
 // k-group of rows keeps the 16-byte stores of 8 consecutive k-groups in
 // distinct banks.
 constexpr uint32_t A_LBO = TM * 16 + 16, B_LBO = TN * 16 + 16;
-constexpr uint32_t A_BYTES = (KR / 4) * A_LBO;   // 16.1 KB
-constexpr uint32_t B_BYTES = (KR / 4) * B_LBO;   //  8.1 KB
-constexpr uint32_t IDESC = tc_idesc(2u, TM, TN);    // TF32 A and B, FP32 accumulator
+
+// Operand formats: TF32 (4-byte elements, core-matrix rows of 4 k-values,
+// MMA K = 8, kind::tf32) or BF16 (2-byte elements, rows of 8 k-values,
+// MMA K = 16, kind::f16 with BF16 inputs).  Both accumulate in FP32.
+template <bool BF> struct Fmt {
+  using E = float;
+  static constexpr int G = 4;                 // k-values per 16-byte core-matrix row
+  static constexpr int MK = 8;                // K of one MMA
+  static constexpr uint32_t IDESC = tc_idesc(2u, TM, TN);
+  static __device__ __forceinline__ E hi(float x, bool split) {
+    return split ? __uint_as_float(__float_as_uint(x) & 0xFFFFE000u) : x;
+  }
+  static __device__ __forceinline__ float val(E x) { return x; }
+  static __device__ __forceinline__ E lo(float x, E h) { return x - h; }
+  static __device__ __forceinline__ void mma(uint32_t t, uint64_t a, uint64_t b, uint32_t acc) {
+    tc_mma_tf32(t, a, b, IDESC, acc);
+  }
+};
+template <> struct Fmt<true> {
+  using E = __nv_bfloat16;
+  static constexpr int G = 8;
+  static constexpr int MK = 16;
+  static constexpr uint32_t IDESC = tc_idesc(1u, TM, TN);
+  static __device__ __forceinline__ E hi(float x, bool) { return __float2bfloat16_rn(x); }
+  static __device__ __forceinline__ float val(E x) { return __bfloat162float(x); }
+  static __device__ __forceinline__ E lo(float x, E h) { return __float2bfloat16_rn(x - __bfloat162float(h)); }
+  static __device__ __forceinline__ void mma(uint32_t t, uint64_t a, uint64_t b, uint32_t acc) {
+    tc_mma_f16(t, a, b, IDESC, acc);
+  }
+};
+
+template <bool BF> constexpr uint32_t a_bytes() { return (KR / Fmt<BF>::G) * A_LBO; }
+template <bool BF> constexpr uint32_t b_bytes() { return (KR / Fmt<BF>::G) * B_LBO; }
 // Shared memory: the two precision halves of A and B plus the barrier.
-constexpr uint32_t SMEM_BYTES = 2 * A_BYTES + 2 * B_BYTES + 16;
+template <bool BF> constexpr uint32_t smem_bytes() { return 2 * a_bytes<BF>() + 2 * b_bytes<BF>() + 16; }
 
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
-
-// element (row r, real k) of a [k/4][rows][4] operand with row groups lbo bytes apart
-__device__ __forceinline__ void put(float* buf, uint32_t lbo, int r, int k, float v) {
-  buf[(k >> 2) * (lbo / 4) + r * 4 + (k & 3)] = v;
+// element (row r, real k) of a [k/G][rows][G] operand with row groups lbo bytes apart
+template <typename E, int G>
+__device__ __forceinline__ void put(E* buf, uint32_t lbo, int r, int k, E v) {
+  buf[(k / G) * (lbo / sizeof(E)) + r * G + (k % G)] = v;
 }
 
-__global__ void __launch_bounds__(128, 4) zgemm_tf32_kernel(const TcGemmJob* jobs, const TcGemmTile* tiles, int split,
-                                                           int* status, long long spin) {
+template <bool BF>
+__global__ void __launch_bounds__(128, 4) zgemm_tc_kernel(const TcGemmJob* jobs, const TcGemmTile* tiles, int split,
+                                                         int* status, long long spin) {
+  using F = Fmt<BF>;
+  using E = typename F::E;
+  constexpr int G = F::G;
+  constexpr uint32_t AB = a_bytes<BF>(), BB = b_bytes<BF>();
   extern __shared__ __align__(1024) unsigned char sm[];
-  float* Ah = reinterpret_cast<float*>(sm);
-  float* Al = reinterpret_cast<float*>(sm + A_BYTES);
-  float* Bh = reinterpret_cast<float*>(sm + 2 * A_BYTES);
-  float* Bl = reinterpret_cast<float*>(sm + 2 * A_BYTES + B_BYTES);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * A_BYTES + 2 * B_BYTES);
+  E* Ah = reinterpret_cast<E*>(sm);
+  E* Al = reinterpret_cast<E*>(sm + AB);
+  E* Bh = reinterpret_cast<E*>(sm + 2 * AB);
+  E* Bl = reinterpret_cast<E*>(sm + 2 * AB + BB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * AB + 2 * BB);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TcGemmTile tl = tiles[blockIdx.x];
@@ -79,29 +116,31 @@ __global__ void __launch_bounds__(128, 4) zgemm_tf32_kernel(const TcGemmJob* job
   const int nchunks = (jb.K + KC - 1) / KC;
   for (int ch = 0; ch < nchunks; ++ch) {
     const int k0 = ch * KC;
-    // A chunk: 128 rows x 8 k-groups of 2 complex (16 bytes); consecutive
-    // threads read consecutive 16-byte pieces of one row (coalesced)
-    for (int e = tid; e < TM * (KC / 2); e += blockDim.x) {
-      const int row = e / (KC / 2), kg = e % (KC / 2);
-      const int m = m0 + row, k = k0 + 2 * kg;
-      c64 v0{0.f, 0.f}, v1{0.f, 0.f};
-      if (m < jb.M) {
-        const c64* ar = A + (long long)m * jb.lda;
-        if (k < jb.K) v0 = ar[k];
-        if (k + 1 < jb.K) v1 = ar[k + 1];
-      }
-      const float x[4] = {v0.re, v0.im, v1.re, v1.im};
-      float hx[4], lx[4];
+    // A chunk: 128 rows x k-groups of G/2 complex (one 16-byte core-matrix
+    // row each); consecutive threads read consecutive pieces of one row
+    constexpr int CG = G / 2;   // complex values per group
+    for (int e = tid; e < TM * (KC / CG); e += blockDim.x) {
+      const int row = e / (KC / CG), kg = e % (KC / CG);
+      const int m = m0 + row, k = k0 + CG * kg;
+      float x[G];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        hx[q] = split ? tf32_hi(x[q]) : x[q];
-        lx[q] = x[q] - hx[q];
+      for (int q = 0; q < CG; ++q) {
+        c64 v{0.f, 0.f};
+        if (m < jb.M && k + q < jb.K) v = A[(long long)m * jb.lda + k + q];
+        x[2 * q] = v.re;
+        x[2 * q + 1] = v.im;
       }
-      *reinterpret_cast<float4*>(Ah + kg * (A_LBO / 4) + row * 4) = make_float4(hx[0], hx[1], hx[2], hx[3]);
+      __align__(16) E hx[G], lx[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        hx[q] = F::hi(x[q], split != 0);
+        lx[q] = F::lo(x[q], hx[q]);
+      }
+      *reinterpret_cast<uint4*>(Ah + kg * (A_LBO / sizeof(E)) + row * G) = *reinterpret_cast<const uint4*>(hx);
       if (split)
-        *reinterpret_cast<float4*>(Al + kg * (A_LBO / 4) + row * 4) = make_float4(lx[0], lx[1], lx[2], lx[3]);
+        *reinterpret_cast<uint4*>(Al + kg * (A_LBO / sizeof(E)) + row * G) = *reinterpret_cast<const uint4*>(lx);
     }
-    // Bt chunk: (k, n) pairs of the chunk, 4 per thread
+    // Bt chunk: (k, n) pairs of the chunk, 4 real entries each
     for (int e = tid; e < KC * TNC; e += blockDim.x) {
       const int kk = e / TNC, nn = e % TNC;
       const int k = k0 + kk, n = n0 + nn;
@@ -111,10 +150,9 @@ __global__ void __launch_bounds__(128, 4) zgemm_tf32_kernel(const TcGemmJob* job
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int row = 2 * nn + (q >> 1), col = 2 * kk + (q & 1);
-        const float x = vals[q];
-        const float h = split ? tf32_hi(x) : x;
-        put(Bh, B_LBO, row, col, h);
-        if (split) put(Bl, B_LBO, row, col, x - h);
+        const E h = F::hi(vals[q], split != 0);
+        put<E, G>(Bh, B_LBO, row, col, h);
+        if (split) put<E, G>(Bl, B_LBO, row, col, F::lo(vals[q], h));
       }
     }
     fence_proxy_async_smem();
@@ -122,13 +160,14 @@ __global__ void __launch_bounds__(128, 4) zgemm_tf32_kernel(const TcGemmJob* job
     if (tid == 0) {
       tc_fence_after();
 #pragma unroll 1
-      for (int kk = 0; kk < KR / 8; ++kk) {
+      for (int kk = 0; kk < KR / F::MK; ++kk) {
+        // one MMA spans two K-adjacent core matrices
         const uint32_t ao = (uint32_t)(2 * kk) * A_LBO, bo = (uint32_t)(2 * kk) * B_LBO;
         const uint32_t first = (ch == 0 && kk == 0) ? 0u : 1u;
-        tc_mma_tf32(tmem, tc_smem_desc(ah + ao, A_LBO, 128u), tc_smem_desc(bh + bo, B_LBO, 128u), IDESC, first);
+        F::mma(tmem, tc_smem_desc(ah + ao, A_LBO, 128u), tc_smem_desc(bh + bo, B_LBO, 128u), first);
         if (split) {
-          tc_mma_tf32(tmem, tc_smem_desc(ah + ao, A_LBO, 128u), tc_smem_desc(bl + bo, B_LBO, 128u), IDESC, 1u);
-          tc_mma_tf32(tmem, tc_smem_desc(al + ao, A_LBO, 128u), tc_smem_desc(bh + bo, B_LBO, 128u), IDESC, 1u);
+          F::mma(tmem, tc_smem_desc(ah + ao, A_LBO, 128u), tc_smem_desc(bl + bo, B_LBO, 128u), 1u);
+          F::mma(tmem, tc_smem_desc(al + ao, A_LBO, 128u), tc_smem_desc(bh + bo, B_LBO, 128u), 1u);
         }
       }
       tc_commit(bar);
@@ -168,7 +207,9 @@ __global__ void __launch_bounds__(128, 4) zgemm_tf32_kernel(const TcGemmJob* job
 
 }  // namespace
 
-int zgemm_tf32_batched(const std::vector<TcGemmJob>& jobs, int split, int* status, long long spin, cudaStream_t s) {
+int zgemm_tc_batched(const std::vector<TcGemmJob>& jobs, int mode, int* status, long long spin, cudaStream_t s) {
+  const bool bf = mode == 2 || mode == 4;
+  const int split = (mode == 3 || mode == 4) ? 1 : 0;
   if (jobs.empty()) return HS_OK;
   std::vector<TcGemmTile> tiles;
   for (int t = 0; t < (int)jobs.size(); ++t)
@@ -185,10 +226,14 @@ int zgemm_tf32_batched(const std::vector<TcGemmJob>& jobs, int split, int* statu
   cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(TcGemmTile), cudaMemcpyHostToDevice, s);
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(zgemm_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    cudaFuncSetAttribute(zgemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<false>());
+    cudaFuncSetAttribute(zgemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<true>());
   });
   note_launch();
-  zgemm_tf32_kernel<<<(int)tiles.size(), 128, SMEM_BYTES, s>>>(dj, dt, split, status, spin);
+  if (bf)
+    zgemm_tc_kernel<true><<<(int)tiles.size(), 128, smem_bytes<true>(), s>>>(dj, dt, split, status, spin);
+  else
+    zgemm_tc_kernel<false><<<(int)tiles.size(), 128, smem_bytes<false>(), s>>>(dj, dt, split, status, spin);
   cudaError_t e = cudaGetLastError();
   cudaError_t e2 = cudaStreamSynchronize(s);
   cudaFree(dj);

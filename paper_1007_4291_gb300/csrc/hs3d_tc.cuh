@@ -1,4 +1,4 @@
-// Batched complex64 GEMMs on the tensor cores (TF32, FP32 accumulation) for
+// Batched complex64 GEMMs on the tensor cores (TF32 or BF16, FP32 accumulation) for
 // the frontal updates of the 3D setup (hs3d_tc.cu).
 #pragma once
 #include <vector>
@@ -16,8 +16,8 @@ struct TcGemmJob {
 };
 struct TcGemmTile { int job, tm, tn; };
 
-// split = 1: 3xTF32 (a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32-level accuracy);
-// 0: one TF32 pass.  Synchronises `s`.
-int zgemm_tf32_batched(const std::vector<TcGemmJob>& jobs, int split, int* status, long long spin, cudaStream_t s);
+// mode 1: one TF32 pass; 3: 3xTF32 (a_hi b_hi + a_hi b_lo + a_lo b_hi,
+// FP32-level accuracy); 2: one BF16 pass; 4: 3xBF16.  Synchronises `s`.
+int zgemm_tc_batched(const std::vector<TcGemmJob>& jobs, int mode, int* status, long long spin, cudaStream_t s);
 
 }  // namespace hs

@@ -197,6 +197,15 @@ extern "C" int hs_destroy(hs_plan* plan) {
   return HS_OK;
 }
 
+extern "C" int hs_setup_flops(const hs_plan* plan, double* gemm_flops, double* inverse_flops) {
+  if (!plan) return HS_EINVAL;
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  const Plan3* q = p->dim == 3 ? static_cast<const Plan3*>(p->p3) : nullptr;
+  if (gemm_flops) *gemm_flops = q ? q->gemm_flops : 0.0;
+  if (inverse_flops) *inverse_flops = q ? q->inv_flops : 0.0;
+  return HS_OK;
+}
+
 extern "C" long long hs_plan_bytes(const hs_plan* plan) {
   if (!plan) return 0;
   const Plan* p = reinterpret_cast<const Plan*>(plan);
@@ -237,7 +246,7 @@ static int prepare_plan3d(const double* c, double omega, int n, int pml_width, i
       opt.max_nrhs > 4096 || opt.restart < 1)
     return HS_EINVAL;
   if (opt.factor_prec != HS_C64 && opt.factor_prec != HS_C128) return HS_EINVAL;
-  if (opt.frontal_gemm != 0 && opt.frontal_gemm != 1 && opt.frontal_gemm != 3) return HS_EINVAL;
+  if (opt.frontal_gemm < 0 || opt.frontal_gemm > 4) return HS_EINVAL;
   if (opt.two_front != 1 || opt.buffer_rows != 0) return HS_EUNSUPPORTED;   // 3D: two fronts, no buffers
   const size_t N3 = (size_t)n * n * n;
   for (size_t k = 0; k < N3; ++k)

@@ -810,6 +810,19 @@ __global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase3_kernel(SweepA
       st2(beta + p * LDR + c0, bv[0], bv[1]);
     }
   }
+  // beta does not change along the chunk: for complex64 windows up to 24 rows
+  // every thread keeps the beta column of its two RHS in registers, so that
+  // the spike correction reads only W_j from shared memory
+  constexpr bool BREG = sizeof(R) == 4 && W <= 24;
+  C bb[BREG ? W : 1][RPT];
+  if constexpr (BREG) {
+    consumer_barrier(NCONS);
+#pragma unroll
+    for (int kk = 0; kk < W; ++kk) {
+      if (has_left) ld2(beta + kk * LDR + c0, bb[kk][0], bb[kk][1]);
+      else bb[kk][0] = bb[kk][1] = C{0, 0};
+    }
+  }
   bool isout[ROWS];
 #pragma unroll
   for (int i = 0; i < ROWS; ++i) isout[i] = (rg + NRG * i >= d.out_off) && (rg + NRG * i < d.out_off + d.d_out);
@@ -865,7 +878,18 @@ __global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase3_kernel(SweepA
       if (isout[i]) {
         const int p = rg + NRG * i;
         C o0 = x[0][i], o1 = x[1][i];
-        if (has_left) {
+        if (BREG && has_left) {
+          const C* vr = V + (p - d.out_off) * LDP;
+#pragma unroll
+          for (int kk = 0; kk < W; kk += 2) {
+            C v0, v1;
+            ld2(vr + kk, v0, v1);
+            cfms(o0, v0, bb[kk][0]);
+            cfms(o1, v0, bb[kk][1]);
+            cfms(o0, v1, bb[BREG ? kk + 1 : 0][0]);
+            cfms(o1, v1, bb[BREG ? kk + 1 : 0][1]);
+          }
+        } else if (has_left) {
           const C* vr = V + (p - d.out_off) * LDP;
 #pragma unroll 4
           for (int kk = 0; kk < W; kk += 2) {

@@ -20,7 +20,7 @@ HS_C64, HS_C128 = 64, 128
 
 EXPORTED = ["hs_default_options", "hs_setup", "hs_setup_batched", "hs_setup_batched_opts", "hs_apply", "hs_apply_batched",
             "hs_apply_noalloc", "hs_autotune", "hs_matvec", "hs_solve", "hs_sync", "hs_last_device_status",
-            "hs_plan_bytes", "hs_release_workspace", "hs_kernel_launches", "hs_destroy", "hs_strerror",
+            "hs_plan_bytes", "hs_setup_flops", "hs_release_workspace", "hs_kernel_launches", "hs_destroy", "hs_strerror",
             "hs_cnn_create", "hs_cnn_get_params", "hs_cnn_set_mode", "hs_cnn_apply", "hs_cnn_gradient",
             "hs_cnn_train_step", "hs_cnn_train_step_residual", "hs_cnn_sync", "hs_cnn_destroy", "hs_attach_cnn"]
 HS_CNN_NPARAM = 10434
@@ -79,6 +79,7 @@ def load(path=None):
     lib.hs_solve.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(HsSolveInfo), vp]
     lib.hs_sync.argtypes = [vp, vp]
     lib.hs_last_device_status.argtypes = [vp]
+    lib.hs_setup_flops.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d)]
     lib.hs_plan_bytes.argtypes = [vp]
     lib.hs_plan_bytes.restype = ll
     lib.hs_destroy.argtypes = [vp]
@@ -314,6 +315,13 @@ def hs_last_device_status(plan):
 
 def hs_plan_bytes(plan):
     return load().hs_plan_bytes(plan)
+
+
+def hs_setup_flops(plan):
+    """(frontal GEMM flops, pivot-block inversion flops) of a 3D plan's setup."""
+    g, v = ctypes.c_double(), ctypes.c_double()
+    _check(load().hs_setup_flops(plan, ctypes.byref(g), ctypes.byref(v)), "hs_setup_flops")
+    return g.value, v.value
 
 
 def hs_destroy(plan):

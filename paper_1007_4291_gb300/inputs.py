@@ -12,14 +12,21 @@ whose formulas are not given in the paper:
 * ``point_sources``: Gaussian point sources exp(-|x-x0|^2/(2 s^2))/(2 pi s^2)
   (unit mass in 2D; (2 pi s^2)^(3/2) in 3D) with s = h, centres uniform in
   [eta, 1-eta]^d.
+* ``waveguide_velocity``: a vertical waveguide with Gaussian cross-section,
+  c = 4/3 (1 - 0.5 exp(-32 (x1 - 1/2)^2)) (the lens profile in x1 only,
+  constant along x2).
+* ``wave_packet``: a Gaussian wave packet exp(-|x-x0|^2/(2 w^2))
+  exp(i k d.(x-x0)), k = omega / c0, with envelope width w equal to one
+  wavelength 2 pi c0 / omega, centred at (0.125, 0.125) and pointing along
+  d = (1, 1)/sqrt(2).
 
 Grids are the paper's: n interior points per axis, h = 1/(n+1), arrays
 indexed [x_d, ..., x_1] with x_1 fastest.
 """
 import numpy as np
 
-__all__ = ["random_velocity", "lens_velocity", "constant_velocity", "point_sources",
-           "centered_source", "random_rhs", "cnn_init_params"]
+__all__ = ["random_velocity", "lens_velocity", "waveguide_velocity", "constant_velocity", "point_sources",
+           "centered_source", "wave_packet", "random_rhs", "cnn_init_params"]
 
 
 def _grid(n):
@@ -51,6 +58,27 @@ def lens_velocity(n, dim=2):
     grids = np.meshgrid(*([x] * dim), indexing="ij")
     r2 = sum((g - 0.5) ** 2 for g in grids)
     return (4.0 / 3.0) * (1.0 - 0.5 * np.exp(-32.0 * r2))
+
+
+def waveguide_velocity(n):
+    """Vertical waveguide (2D): the lens profile in x1 only, constant along x2."""
+    _, x = _grid(n)
+    c1 = (4.0 / 3.0) * (1.0 - 0.5 * np.exp(-32.0 * (x - 0.5) ** 2))
+    return np.tile(c1[None, :], (n, 1))
+
+
+def wave_packet(n, omega, center=(0.125, 0.125), direction=(1.0, 1.0), c0=1.0):
+    """Gaussian wave packet (2D, complex128, shape (1, n, n)): envelope of one
+    wavelength width at ``center``, plane-wave phase along ``direction``."""
+    _, x = _grid(n)
+    X2, X1 = np.meshgrid(x, x, indexing="ij")
+    k = omega / c0
+    w = 2 * np.pi * c0 / omega
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    r1, r2 = X1 - center[0], X2 - center[1]
+    f = np.exp(-(r1 ** 2 + r2 ** 2) / (2 * w ** 2)) * np.exp(1j * k * (d[0] * r1 + d[1] * r2))
+    return f.astype(np.complex128)[None]
 
 
 def constant_velocity(n, dim=2, value=1.0):

@@ -178,3 +178,27 @@ def test_variant_options_are_checked():
     with pytest.raises(hs.HsError) as e:
         hs.hs_setup(c3.ravel(), 10.0, 9, 3, 2, 2, o)
     assert e.value.code == hs.HS_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("velocity", ["waveguide", "lens"])
+def test_paper_workload_wave_packet_solve(velocity):
+    """Sec. 3 Test 2 on the GPU: the Gaussian wave packet from (0.125, 0.125)
+    along (1, 1) in the vertical waveguide and in the lens, n = 255 at 16
+    points per wavelength, solved to 1e-6 under the oracle's FP64 operator."""
+    n, bp = 255, 12
+    omega = 2 * np.pi * 16.0
+    c = I.waveguide_velocity(n) if velocity == "waveguide" else I.lens_velocity(n)
+    f = I.wave_packet(n, omega)
+    o = hs.hs_default_options(alpha=2.0, pml_C=C_PML, layers_per_step=12, max_nrhs=1)
+    plan = hs.hs_setup(c.ravel(), omega, n, 2, bp, bp, o)
+    try:
+        fg = torch.from_numpy(f).to("cuda")
+        ug = torch.zeros_like(fg)
+        code, info = hs.hs_solve(plan, fg, ug, 1, 1e-6, 200)
+        assert code == hs.HS_OK, info
+        A0 = H.helmholtz_matrix(c, omega, bp, C_PML, 0.0)
+        u = ug.cpu().numpy()[0]
+        assert np.linalg.norm(f[0].ravel() - A0 @ u.ravel()) <= 1e-6 * np.linalg.norm(f[0].ravel())
+        assert info["iterations"] <= 30
+    finally:
+        hs.hs_destroy(plan)

@@ -440,3 +440,39 @@ def test_moving_pml_planted_slips_fail_green_pin(monkeypatch, slip):
     }[slip]
     monkeypatch.setattr(S, "moving_sigma", planted)
     assert not _half_space_pin_holds(_half_space_errors("lower"))
+
+
+@pytest.mark.parametrize("velocity,table", [("lens", "2DPML1"), ("waveguide", "2DPML2"), ("random", "2DPML3")])
+@pytest.mark.parametrize("test", [1, 2])
+def test_behaviour_paper_workloads(velocity, table, test):
+    """Sec. 3, the paper's grid of workloads at q = 8 points per wavelength,
+    n = 127 (omega/2pi = 16), alpha = 2, b = d = 12, left GMRES to 1e-3:
+    velocity fields lens / vertical waveguide / random, forces Test 1 (point
+    source at (0.5, 0.125)) and Test 2 (wave packet from (0.125, 0.125) along
+    (1, 1)).  Synthetic stand-ins for the paper's fields: the iteration count
+    must stay within the paper's count for the same table and test."""
+    with open(os.path.join(GOLDEN, "paper_2d_iterations.json")) as fh:
+        gold = json.load(fh)
+    rows = [r for t in gold["tables"] if t["table"] == table for r in t["rows"] if r["n"] == 127 and r["test"] == test]
+    assert len(rows) == 1
+    n, omega = 127, 2 * np.pi * 16
+    c = {"lens": I.lens_velocity(n), "waveguide": I.waveguide_velocity(n), "random": I.random_velocity(n, 0)}[velocity]
+    f = (I.centered_source(n, center=(0.5, 0.125)) if test == 1 else I.wave_packet(n, omega))[0]
+    A0 = H.helmholtz_matrix(c, omega, 12, 20.0, 0.0)
+    st = S.setup(c, omega, 12, 12, 12, 2.0, 20.0)
+    P = lambda v: S.apply(st, v.reshape(n, n)).ravel()
+    _, it, _ = K.gmres_left(lambda v: A0 @ v, P, f.ravel(), tol=1e-3, maxit=200)
+    assert 1 <= it <= rows[0]["n_iter"]
+
+
+def test_workload_inputs_shapes():
+    """The waveguide is constant along x2 and slowest on x1 = 1/2; the packet
+    has unit peak amplitude at its centre and one wavelength of envelope."""
+    n = 63
+    c = I.waveguide_velocity(n)
+    assert np.allclose(c, c[0:1, :])
+    assert np.argmin(c[0]) == (n - 1) // 2
+    f = I.wave_packet(n, 2 * np.pi * 8)[0]
+    h = 1.0 / (n + 1)
+    j = int(round(0.125 / h)) - 1
+    assert abs(abs(f[j, j]) - 1.0) < 1e-12
