@@ -587,6 +587,57 @@ def paper_workloads(stream, ns=(1023, 2047), tol=1e-3):
     return out
 
 
+CNN_WEIGHTS = os.path.join(ROOT, "paper_1007_4291_gb300", "cnn_weights_n511.npy")
+
+
+def learned_correction(stream, ns=(511, 1023), nrhs=64, tol=1e-6):
+    """The learned post-correction on held-out fields (velocity seeds 5000+n,
+    64 point sources, seeds 7000+n), n = 511 and 1023 at 16 points per
+    wavelength: FGMRES iterations and time-to-1e-6 for the plain sweep in the
+    default refinement solver, the plain sweep in the double-float-basis
+    solver (the one the network runs in), and the sweep with the network
+    attached (its correction judged per direction and RHS by the FP64
+    residual).  The network's weights were trained on pairs made by the method
+    on n = 511 fields (train_cnn.py) and are read from the package."""
+    import torch
+    from paper_1007_4291_gb300 import hs
+    from paper_1007_4291_gb300 import inputs as I
+    if not os.path.exists(CNN_WEIGHTS):
+        return {"unavailable": "no trained weights in the package"}
+    net = hs.hs_cnn_create(np.load(CNN_WEIGHTS))
+    out = {"what": "held-out fields, %d RHS, tol %g" % (nrhs, tol), "runs": []}
+    try:
+        hs.hs_cnn_set_mode(net, 1)
+        for n in ns:
+            c = np.ascontiguousarray(I.random_velocity(n, 5000 + n).ravel())
+            f = torch.from_numpy(I.point_sources(n, nrhs, 7000 + n, 12)).to("cuda")
+            omega = 2 * np.pi * (n + 1) / 16.0
+            for name, kb, use in (("plain_refinement", 1, False), ("plain_double_float_basis", 0, False),
+                                  ("network_double_float_basis", 0, True)):
+                opt = hs.hs_default_options(layers_per_step=12, max_nrhs=nrhs, krylov_basis=kb)
+                rec = None
+                for _ in range(2):
+                    u = torch.zeros_like(f)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    plan = hs.hs_setup(c, omega, n, 2, 12, 12, opt, stream)
+                    if use:
+                        hs.hs_attach_cnn(plan, net)
+                    code, info = hs.hs_solve(plan, f, u, nrhs, tol, 300, stream)
+                    torch.cuda.synchronize()
+                    t1 = time.perf_counter()
+                    hs.hs_destroy(plan)
+                    rec = {"n": n, "solver": name, "status": code, "iterations": info["iterations"],
+                           "time_to_tol_s": t1 - t0, "max_relres": info["max_relres"],
+                           "corrections_kept": info["cnn_applies"]}
+                out["runs"].append(rec)
+            del f
+            hs.hs_release_workspace()
+    finally:
+        hs.hs_cnn_destroy(net)
+    return out
+
+
 def aggregate(ms_local, world, nrhs, dist=None, device="cpu"):
     """Whole-job figures of a replica run: the slowest rank's time per step
     (MAX over ranks) and the RHS solved per second by all ranks together."""
@@ -749,6 +800,7 @@ def run_ours(args):
             "same workload and tolerance", moving_pml_C=2.0 * wl["C"])
         line["comparator_fp64"] = comparator_fp64(args, wl, stream)
         line["paper_workloads"] = paper_workloads(stream)
+        line["learned_correction"] = learned_correction(stream)
         line["batched_uneven"] = batched_uneven(stream)
         line["three_d"] = three_d(stream)
     if rank == 0 and world == 1 and not args.no_cpu:

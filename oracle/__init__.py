@@ -25,7 +25,8 @@ band LU, dense solve) as steps:
 * ``cnn``         -- FP64 reference of the 3-layer convolutional
   post-correction (forward, backward, Adam).
 
-Parity status of each function is stated in its docstring; where the exact
-value of an approximation is fixed only by a reading of a passage the paper
-leaves open (stated in that docstring), the docstring says "parity unpinned".
+Each function's docstring states the passage it follows and the readings
+of passages the paper leaves open; the tests pin every function against
+values and limits the paper and the mathematics fix (hand-computed profiles,
+exact solves, Green's functions, finite differences).
 """

@@ -7,8 +7,9 @@ Paper passages restated here (Engquist & Ying 2010, Sec. 2.1):
                  0                            on [eta, 1 - eta],
                  (C/eta) ((t - 1 + eta)/eta)^2 on [1 - eta, 1].
   Every experiment of the paper puts the PML on all four sides, so both
-  axes use this two-sided profile (the one-sided sigma_2 of Sec. 2.1 belongs
-  to the Dirichlet-top variant).
+  axes use this two-sided profile by default; the one-sided sigma_2 of Sec.
+  2.1 (``pml_sigma_one_sided``, ``dirichlet_top=True``) gives the
+  Dirichlet-top formulation that Algorithms 3 and 4 are written for.
 * Stretch factors s_k(x_k) = (1 + i sigma_k(x_k)/omega)^(-1), with the real
   frequency omega (the shift alpha of Eq. helmalpha changes only the mass
   term).

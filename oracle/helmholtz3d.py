@@ -23,10 +23,11 @@ Restates Sec. 4 of Engquist & Ying (2010):
 
 The block partition, the moving profile and the window rules are those of
 ``sweep2d`` with rows read as x3 layers; they are reused from there.  The
-readings listed there apply here unchanged.  The exact value of M_alpha for
-moving-PML windows is "parity unpinned" beyond the exact limits the tests pin
-(full windows reproduce A_alpha^{-1}; exact Schur complements reproduce a
-sparse direct solve).
+readings listed there apply here unchanged.  Pins: the x3 moving profile is
+the 2D one (its hand-computed values are checked through
+``window_x3_stretch``); full windows reproduce A_alpha^{-1}; exact Schur
+complements reproduce a sparse direct solve; the Green's function
+-exp(ikr)/(4 pi r) converges at second order.
 """
 from dataclasses import dataclass
 

@@ -32,10 +32,19 @@ path, chosen independently there):
   - the half band width of P_m H_m P_m^t is the window height (the paper's
     "b - 1 diagonals" is an off-by-one);
   - the LAPACK band LU pivots by rows; any exact solver defines the same T~.
-The exact value of M_alpha for a moving-PML window is therefore
-"parity unpinned" beyond the exact limits pinned by the tests (full-window
-mode reproduces A_alpha^{-1}; exact Schur complements reproduce a sparse
-direct solve).
+* Sec. 2.1-2.2 as printed (``partition_single``, ``two_front=False``): the
+  Dirichlet-top formulation, one-sided sigma_2, one upward sweep from F, the
+  top block solved once (no middle layer).
+* Sec. 2.2, buffer layers (``buffer``): k undamped rows between a block and
+  its moving PML; a window that would cross the grid boundary is cut there
+  and keeps the operator's own profile (the exact Schur inverse).
+
+Pins (tests/): the moving profile against hand-computed values (b != b_p,
+lower, upper and middle windows, with and without buffers) and against the
+half-space Green's function it approximates (error falling in b and in k);
+each T~ against a dense solve of H_B; the sweep algebra against sparse direct
+solves in its exact limits (full windows, exact Schur complements, windows
+cut by large buffers), for both formulations.
 """
 from dataclasses import dataclass
 import numpy as np
