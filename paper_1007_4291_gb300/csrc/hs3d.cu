@@ -247,12 +247,16 @@ __global__ void __launch_bounds__(512) invert_kernel(const SetupItem* items, cpl
       rowk[i] = (i == k) ? pinv : cmul(A[(long long)k * LD + i], pinv);
     }
     __syncthreads();
-    for (long long e = threadIdx.x; e < (long long)S * S; e += blockDim.x) {
-      const int i = (int)(e / S), j = (int)(e % S);
-      C& x = A[(long long)i * LD + j];
-      if (i == k) x = rowk[j];
-      else if (j == k) x = cmul(C{-colk[i].re, -colk[i].im}, pinv);
-      else x = csub(x, cmul(colk[i], rowk[j]));
+    // rank-1 update: rows over warps, columns over lanes (coalesced rows)
+    const int nw = (int)(blockDim.x >> 5), lane = threadIdx.x & 31;
+    for (int i = (int)(threadIdx.x >> 5); i < S; i += nw) {
+      C* Ai = A + (long long)i * LD;
+      const C ci = colk[i];
+      if (i == k) {
+        for (int j = lane; j < S; j += 32) Ai[j] = rowk[j];
+      } else {
+        for (int j = lane; j < S; j += 32) Ai[j] = (j == k) ? cmul(C{-ci.re, -ci.im}, pinv) : csub(Ai[j], cmul(ci, rowk[j]));
+      }
     }
     __syncthreads();
   }
