@@ -79,8 +79,9 @@ typedef struct {
   int frontal_gemm;      /* 3D setup, frontal Schur updates of complex64 factors (Sec. 4.2): 0 CUDA-
                             core FP32 FMA; tensor cores with FP32 accumulation: 1 TF32 (one pass),
                             3 3xTF32 (split operands, FP32-level accuracy), 2 BF16 (one pass),
-                            4 3xBF16 (split operands, about 16 significant bits).  Complex128
-                            factors use FP64 FMA.                                             default 3 */
+                            4 3xBF16 (split operands, about 16 significant bits).  The blocked
+                            inverse of large front pivot blocks uses the split form of the same
+                            operand type.  Complex128 factors use FP64 FMA.                   default 3 */
   const char* tune_cache;/* path of the table written by hs_autotune; with chunk = 0, hs_setup
                             takes the chunk length (and, with sep_rhs_per_cta = 0, the separator
                             grouping) from it when it holds the problem's key.  NULL: not used.

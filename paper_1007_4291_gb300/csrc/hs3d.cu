@@ -585,6 +585,284 @@ void release_plan3(Plan& p) {
   p.p3 = nullptr;
 }
 
+// Blocked Gauss-Jordan inverse of the large front pivot blocks (S > 64): the
+// same partial pivoting by rows and the same in-place result as
+// invert_kernel, with the work of every NB-column panel split in two.
+//  * panel_kernel: the panel's NB pivot steps on its own columns only (one
+//    CTA per front, rows over warps, one lane per panel column): pivot search
+//    over rows >= k, row swap inside the panel, Gauss-Jordan update.  The
+//    panel columns then hold E[:, P], the columns of the panel's accumulated
+//    transformation E = I + (E[:, P] - I[:, P]) e_P^t.
+//  * swap_rest_kernel applies the panel's row swaps to every other column,
+//    copy_rows_kernel saves the pivot rows T = A[P, :], and the deferred
+//    update of the other columns is two batched GEMMs:
+//      A[i, c] += E[i, P] T[:, c]   (i not in P),   A[P, c] = E[P, P] T[:, c]
+//    run by the frontal-update GEMM path (tensor cores, in the split form of
+//    the chosen operand type, or FMA).
+//  * unpivot_kernel undoes the row pivoting by column swaps at the end.
+constexpr int INV_NB = 32;        // panel width
+constexpr int INV_DIRECT = 64;    // fronts up to this size keep the one-kernel inverse
+
+template <typename R>
+__global__ void __launch_bounds__(512) panel_kernel(const SetupItem* items, cplx<R>* F, int k0, int* piv_all,
+                                                    const long long* piv_off, int* status) {
+  using C = cplx<R>;
+  __shared__ C rowk[INV_NB];
+  __shared__ R bestv[16];
+  __shared__ int besti[16];
+  __shared__ int pr_s;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* colk = reinterpret_cast<C*>(smraw);
+  const SetupItem it = items[blockIdx.x];
+  const int S = it.S, LD = it.S + it.Bd;
+  if (k0 >= S) return;
+  const int kb = min(INV_NB, S - k0);
+  C* A = F + it.f_off;
+  int* piv = piv_all + piv_off[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  bool ok = true;
+  for (int kk = 0; kk < kb; ++kk) {
+    const int k = k0 + kk;
+    R v = R(-1);
+    int idx = k;
+    for (int i = k + threadIdx.x; i < S; i += blockDim.x) {
+      const R a = cabs2(A[(long long)i * LD + k]);
+      if (a > v) { v = a; idx = i; }
+    }
+    for (int m = 16; m > 0; m >>= 1) {
+      const R ov = Shfl<R>::xr(v, m);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, m);
+      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    if (lane == 0) { bestv[warp] = v; besti[warp] = idx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      R bv = bestv[0];
+      int bi = besti[0];
+      for (int q = 1; q < nw; ++q)
+        if (bestv[q] > bv || (bestv[q] == bv && besti[q] < bi)) { bv = bestv[q]; bi = besti[q]; }
+      if (!(bv > R(0)) || !isfinite(bv)) { ok = false; bi = k; }
+      pr_s = bi;
+      piv[k] = bi;
+    }
+    __syncthreads();
+    const int pr = pr_s;
+    if (pr != k && threadIdx.x < kb) {
+      C* a = A + (long long)k * LD + k0 + threadIdx.x;
+      C* b = A + (long long)pr * LD + k0 + threadIdx.x;
+      const C t = *a;
+      *a = *b;
+      *b = t;
+    }
+    __syncthreads();
+    const C pinv = cinv(A[(long long)k * LD + k]);
+    for (int i = threadIdx.x; i < S; i += blockDim.x) colk[i] = A[(long long)i * LD + k];
+    if (threadIdx.x < kb) rowk[threadIdx.x] = (threadIdx.x == kk) ? pinv : cmul(A[(long long)k * LD + k0 + threadIdx.x], pinv);
+    __syncthreads();
+    if (lane < kb)
+      for (int i = warp; i < S; i += nw) {
+        C& x = A[(long long)i * LD + k0 + lane];
+        if (i == k) x = rowk[lane];
+        else if (lane == kk) x = cmul(C{-colk[i].re, -colk[i].im}, pinv);
+        else x = csub(x, cmul(colk[i], rowk[lane]));
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && !ok) set_status(status, HS_EBREAKDOWN, it.block, it.node);
+}
+
+// the panel's row swaps (in order) on every column outside the panel
+template <typename R>
+__global__ void __launch_bounds__(256) swap_rest_kernel(const SetupItem* items, cplx<R>* F, int k0, const int* piv_all,
+                                                        const long long* piv_off) {
+  using C = cplx<R>;
+  const SetupItem it = items[blockIdx.x];
+  const int S = it.S, LD = it.S + it.Bd;
+  if (k0 >= S) return;
+  const int kb = min(INV_NB, S - k0);
+  C* A = F + it.f_off;
+  const int* piv = piv_all + piv_off[blockIdx.x];
+  for (int kk = 0; kk < kb; ++kk) {
+    const int k = k0 + kk, pr = piv[k];
+    if (pr != k)
+      for (int j = threadIdx.x; j < S; j += blockDim.x) {
+        if (j >= k0 && j < k0 + kb) continue;
+        const C t = A[(long long)k * LD + j];
+        A[(long long)k * LD + j] = A[(long long)pr * LD + j];
+        A[(long long)pr * LD + j] = t;
+      }
+    __syncthreads();
+  }
+}
+
+// T[q][j] = A[k0 + q][j], the panel's pivot rows before the deferred update
+template <typename R>
+__global__ void __launch_bounds__(256) copy_rows_kernel(const SetupItem* items, const cplx<R>* F, int k0,
+                                                        cplx<R>* T, const long long* t_off) {
+  const SetupItem it = items[blockIdx.x];
+  const int S = it.S, LD = it.S + it.Bd;
+  if (k0 >= S) return;
+  const int kb = min(INV_NB, S - k0);
+  const cplx<R>* A = F + it.f_off;
+  cplx<R>* Tb = T + t_off[blockIdx.x];
+  for (int e = threadIdx.x; e < kb * S; e += blockDim.x) {
+    const int q = e / S, j = e - q * S;
+    Tb[e] = A[(long long)(k0 + q) * LD + j];
+  }
+}
+
+// undo the row pivoting: column swaps in reverse order
+template <typename R>
+__global__ void __launch_bounds__(256) unpivot_kernel(const SetupItem* items, cplx<R>* F, const int* piv_all,
+                                                      const long long* piv_off) {
+  using C = cplx<R>;
+  const SetupItem it = items[blockIdx.x];
+  const int S = it.S, LD = it.S + it.Bd;
+  C* A = F + it.f_off;
+  const int* piv = piv_all + piv_off[blockIdx.x];
+  for (int k = S - 1; k >= 0; --k) {
+    const int pr = piv[k];
+    if (pr != k)
+      for (int i = threadIdx.x; i < S; i += blockDim.x) {
+        const C t = A[(long long)i * LD + k];
+        A[(long long)i * LD + k] = A[(long long)i * LD + pr];
+        A[(long long)i * LD + pr] = t;
+      }
+    __syncthreads();
+  }
+}
+
+// Host side of the blocked inverse for the large fronts of one tree level.
+// All panels' GEMM jobs are formed up front (their operands sit at fixed
+// places) and uploaded once; the level is synchronised by the caller.
+template <typename R>
+int blocked_inverse(Plan& p, const std::vector<SetupItem>& large, cplx<R>* F, cudaStream_t s) {
+  using C = cplx<R>;
+  const int nl = (int)large.size();
+  if (nl == 0) return HS_OK;
+  int Smax = 0;
+  std::vector<long long> piv_off(nl), t_off(nl);
+  long long ptot = 0, ttot = 0;
+  for (int i = 0; i < nl; ++i) {
+    Smax = std::max(Smax, large[i].S);
+    piv_off[i] = ptot; ptot += large[i].S;
+    t_off[i] = ttot; ttot += (long long)INV_NB * large[i].S;
+  }
+  const bool tc = sizeof(R) == 4 && p.opt.frontal_gemm != 0;
+  const int npan = (Smax + INV_NB - 1) / INV_NB;
+  // GEMM jobs of every panel: rows outside the panel (A += E[R, P] T[:, c])
+  // and the panel rows (A[P, c] = E[P, P] T[:, c]), columns outside the panel
+  std::vector<GemmJob> gj;
+  std::vector<GemmTile> gt;
+  std::vector<TcGemmJob> tj;
+  std::vector<TcGemmTile> tt;
+  std::vector<int> pan_tile(npan + 1, 0);
+  for (int pn = 0; pn < npan; ++pn) {
+    const int k0 = pn * INV_NB;
+    std::vector<GemmJob> jobs;
+    for (int i = 0; i < nl; ++i) {
+      const SetupItem& it = large[i];
+      const int S = it.S, LD = it.S + it.Bd;
+      if (k0 >= S) continue;
+      const int kb = std::min(INV_NB, S - k0);
+      C* A = F + it.f_off;
+      C* Tb = nullptr;   // device address formed after allocation: offset kept in ldb-free form below
+      (void)Tb;
+      const int rr[2][2] = {{0, k0}, {k0 + kb, S}};
+      for (auto& cr : rr) {
+        const int c0 = cr[0], nc = cr[1] - cr[0];
+        if (nc <= 0) continue;
+        for (auto& rw : rr) {
+          const int r0 = rw[0], nr = rw[1] - rw[0];
+          if (nr <= 0) continue;
+          // B operand recorded as an offset into T; fixed up below
+          jobs.push_back(GemmJob{A + (long long)r0 * LD + k0, reinterpret_cast<void*>(t_off[i] + c0), A + (long long)r0 * LD + c0,
+                                 LD, S, LD, nr, nc, kb, 1, 1});
+        }
+        jobs.push_back(GemmJob{A + (long long)k0 * LD + k0, reinterpret_cast<void*>(t_off[i] + c0), A + (long long)k0 * LD + c0,
+                               LD, S, LD, kb, nc, kb, 1, 0});
+      }
+    }
+    for (auto& j : jobs) {
+      if (tc) {
+        TcGemmJob t{j.A, j.B, j.C, j.lda, j.ldb, j.ldc, j.M, j.N, j.K, (float)j.alpha, j.beta};
+        tj.push_back(t);
+      } else {
+        gj.push_back(j);
+      }
+    }
+    pan_tile[pn + 1] = pan_tile[pn];
+    if (tc) {
+      const size_t before = tt.size();
+      std::vector<TcGemmJob> last(tj.end() - jobs.size(), tj.end());
+      zgemm_tc_tiles(last, (int)(tj.size() - jobs.size()), tt);
+      pan_tile[pn + 1] += (int)(tt.size() - before);
+    } else {
+      for (int t = (int)(gj.size() - jobs.size()); t < (int)gj.size(); ++t)
+        for (int tm = 0; tm < (gj[t].M + 63) / 64; ++tm)
+          for (int tn = 0; tn < (gj[t].N + 63) / 64; ++tn) {
+            gt.push_back({t, tm, tn});
+            ++pan_tile[pn + 1];
+          }
+    }
+  }
+  SetupItem* d_items = nullptr;
+  int* d_piv = nullptr;
+  long long *d_poff = nullptr, *d_toff = nullptr;
+  C* d_T = nullptr;
+  void* d_jobs = nullptr;
+  void* d_tiles = nullptr;
+  const size_t njob = tc ? tj.size() : gj.size(), ntile = tc ? tt.size() : gt.size();
+  const size_t jsz = tc ? sizeof(TcGemmJob) : sizeof(GemmJob), tsz = tc ? sizeof(TcGemmTile) : sizeof(GemmTile);
+  int st = HS_OK;
+  if (cudaMalloc(&d_items, nl * sizeof(SetupItem)) != cudaSuccess || cudaMalloc(&d_piv, ptot * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&d_poff, nl * sizeof(long long)) != cudaSuccess || cudaMalloc(&d_toff, nl * sizeof(long long)) != cudaSuccess ||
+      cudaMalloc(&d_T, std::max<long long>(ttot, 1) * sizeof(C)) != cudaSuccess ||
+      cudaMalloc(&d_jobs, std::max<size_t>(njob, 1) * jsz) != cudaSuccess ||
+      cudaMalloc(&d_tiles, std::max<size_t>(ntile, 1) * tsz) != cudaSuccess) {
+    cudaGetLastError();
+    st = HS_ENOMEM;
+  }
+  if (st == HS_OK) {
+    // B operands: offsets into T -> device addresses
+    for (auto& j : gj) j.B = d_T + reinterpret_cast<long long>(j.B);
+    for (auto& j : tj) j.B = d_T + reinterpret_cast<long long>(j.B);
+    cudaMemcpyAsync(d_items, large.data(), nl * sizeof(SetupItem), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_poff, piv_off.data(), nl * sizeof(long long), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_toff, t_off.data(), nl * sizeof(long long), cudaMemcpyHostToDevice, s);
+    if (njob) cudaMemcpyAsync(d_jobs, tc ? (const void*)tj.data() : (const void*)gj.data(), njob * jsz, cudaMemcpyHostToDevice, s);
+    if (ntile) cudaMemcpyAsync(d_tiles, tc ? (const void*)tt.data() : (const void*)gt.data(), ntile * tsz, cudaMemcpyHostToDevice, s);
+    const size_t psm = (size_t)Smax * sizeof(C);
+    if (psm > 48 * 1024) cudaFuncSetAttribute(panel_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+    for (int pn = 0; pn < npan && st == HS_OK; ++pn) {
+      const int k0 = pn * INV_NB;
+      note_launch(3);
+      panel_kernel<R><<<nl, 512, psm, s>>>(d_items, F, k0, d_piv, d_poff, p.d_status);
+      swap_rest_kernel<R><<<nl, 256, 0, s>>>(d_items, F, k0, d_piv, d_poff);
+      copy_rows_kernel<R><<<nl, 256, 0, s>>>(d_items, F, k0, d_T, d_toff);
+      const int t0 = pan_tile[pn], tn = pan_tile[pn + 1] - pan_tile[pn];
+      if (tn > 0) {
+        if (tc) {
+          // the inverse keeps FP32-level accuracy: the split form of the mode's operand type
+          const int mode = p.opt.frontal_gemm == 1 ? 3 : p.opt.frontal_gemm == 2 ? 4 : p.opt.frontal_gemm;
+          st = zgemm_tc_launch(static_cast<const TcGemmJob*>(d_jobs), static_cast<const TcGemmTile*>(d_tiles) + t0, tn,
+                               mode, p.d_status, p.opt.spin_budget, s);
+        } else {
+          note_launch();
+          gemm_kernel<R><<<tn, 256, 0, s>>>(static_cast<const GemmJob*>(d_jobs), static_cast<const GemmTile*>(d_tiles) + t0);
+        }
+      }
+    }
+    note_launch();
+    unpivot_kernel<R><<<nl, 256, 0, s>>>(d_items, F, d_piv, d_poff);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (st == HS_OK && e != cudaSuccess) st = cuda_status(e);
+  }
+  for (void* x : {(void*)d_items, (void*)d_piv, (void*)d_poff, (void*)d_toff, (void*)d_T, d_jobs, d_tiles})
+    if (x) cudaFree(x);
+  return st;
+}
+
 template <typename R>
 int setup3_t(Plan& p, Plan3& q, cudaStream_t s) {
   using C = cplx<R>;
@@ -643,10 +921,30 @@ int setup3_t(Plan& p, Plan3& q, cudaStream_t s) {
     note_launch();
     assemble_kernel<R><<<(int)its.size(), 256, 0, s>>>(cf, p.d_blocks, q.d_nodes, d_its, (C*)F, prevItems,
                                                         (const C*)prevF);
-    const size_t ism = (size_t)Smax * 2 * es + (size_t)Smax * sizeof(int);
-    if (ism > 48 * 1024) cudaFuncSetAttribute(invert_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
-    note_launch();
-    invert_kernel<R><<<(int)its.size(), 512, ism, s>>>(d_its, (C*)F, p.d_status);
+    // pivot-block inverses: one kernel for the small fronts, the blocked
+    // Gauss-Jordan (panels + GEMM updates) for the large ones
+    {
+      std::vector<SetupItem> small, large;
+      int Ssmall = 0;
+      for (auto& it : its) {
+        if (it.S > INV_DIRECT) large.push_back(it);
+        else { small.push_back(it); Ssmall = std::max(Ssmall, it.S); }
+      }
+      SetupItem* d_small = nullptr;
+      if (!small.empty()) {
+        if (cudaMalloc(&d_small, small.size() * sizeof(SetupItem)) != cudaSuccess) { cudaGetLastError(); st = HS_ENOMEM; }
+        else {
+          cudaMemcpyAsync(d_small, small.data(), small.size() * sizeof(SetupItem), cudaMemcpyHostToDevice, s);
+          const size_t ism = (size_t)Ssmall * 2 * es + (size_t)Ssmall * sizeof(int);
+          if (ism > 48 * 1024) cudaFuncSetAttribute(invert_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
+          note_launch();
+          invert_kernel<R><<<(int)small.size(), 512, ism, s>>>(d_small, (C*)F, p.d_status);
+        }
+      }
+      if (st == HS_OK) st = blocked_inverse<R>(p, large, (C*)F, s);
+      if (d_small) { cudaStreamSynchronize(s); cudaFree(d_small); }
+      if (st != HS_OK) { cudaFree(F); cudaFree(d_its); break; }
+    }
     // L = F21 G ; F22 -= L F12
     std::vector<GemmJob> j1, j2;
     for (auto& it : its) {

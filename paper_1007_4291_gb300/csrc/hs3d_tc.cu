@@ -207,6 +207,31 @@ __global__ void __launch_bounds__(128, 4) zgemm_tc_kernel(const TcGemmJob* jobs,
 
 }  // namespace
 
+int zgemm_tc_launch(const TcGemmJob* d_jobs, const TcGemmTile* d_tiles, int ntiles, int mode, int* status,
+                    long long spin, cudaStream_t s) {
+  if (ntiles <= 0) return HS_OK;
+  const bool bf = mode == 2 || mode == 4;
+  const int split = (mode == 3 || mode == 4) ? 1 : 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(zgemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<false>());
+    cudaFuncSetAttribute(zgemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<true>());
+  });
+  note_launch();
+  if (bf)
+    zgemm_tc_kernel<true><<<ntiles, 128, smem_bytes<true>(), s>>>(d_jobs, d_tiles, split, status, spin);
+  else
+    zgemm_tc_kernel<false><<<ntiles, 128, smem_bytes<false>(), s>>>(d_jobs, d_tiles, split, status, spin);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HS_OK : cuda_status(e);
+}
+
+void zgemm_tc_tiles(const std::vector<TcGemmJob>& jobs, int job0, std::vector<TcGemmTile>& tiles) {
+  for (int t = 0; t < (int)jobs.size(); ++t)
+    for (int tm = 0; tm < (jobs[t].M + TM - 1) / TM; ++tm)
+      for (int tn = 0; tn < (jobs[t].N + TNC - 1) / TNC; ++tn) tiles.push_back({job0 + t, tm, tn});
+}
+
 int zgemm_tc_batched(const std::vector<TcGemmJob>& jobs, int mode, int* status, long long spin, cudaStream_t s) {
   const bool bf = mode == 2 || mode == 4;
   const int split = (mode == 3 || mode == 4) ? 1 : 0;

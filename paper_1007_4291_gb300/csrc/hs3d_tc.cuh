@@ -19,5 +19,11 @@ struct TcGemmTile { int job, tm, tn; };
 // mode 1: one TF32 pass; 3: 3xTF32 (a_hi b_hi + a_hi b_lo + a_lo b_hi,
 // FP32-level accuracy); 2: one BF16 pass; 4: 3xBF16.  Synchronises `s`.
 int zgemm_tc_batched(const std::vector<TcGemmJob>& jobs, int mode, int* status, long long spin, cudaStream_t s);
+// The same on job and tile lists already on the device (no allocation, no
+// synchronisation); zgemm_tc_tiles appends the tiles of `jobs`, numbered
+// from job0, to `tiles`.
+int zgemm_tc_launch(const TcGemmJob* d_jobs, const TcGemmTile* d_tiles, int ntiles, int mode, int* status,
+                    long long spin, cudaStream_t s);
+void zgemm_tc_tiles(const std::vector<TcGemmJob>& jobs, int job0, std::vector<TcGemmTile>& tiles);
 
 }  // namespace hs
