@@ -148,11 +148,14 @@ __device__ __forceinline__ void ring_producer(uint64_t* full, uint64_t* empty, i
 // vector being carried from shared memory (written by its owners before a
 // named barrier), so every column costs one barrier.  A producer warp streams
 // the column payloads.
-template <typename R, int W> struct Tile13 {
-  static constexpr int ROWS = (W == 12) ? 3 : W / 8;  // window rows per thread
+// SM: the small tile for at most 16 right-hand sides: CTAs of 16 RHS, one
+// window row per thread, so that the per-column chain of a thread (which sets
+// the pace when few warps share an SM) is a third as long.
+template <typename R, int W, bool SM = false> struct Tile13 {
+  static constexpr int ROWS = SM ? 1 : (W == 12) ? 3 : W / 8;  // window rows per thread
   static constexpr int NRG = W / ROWS;                // row groups
   static constexpr int RPT = 2;                       // RHS per thread
-  static constexpr int RG = sizeof(R) == 4 ? 64 : 32; // RHS per CTA
+  static constexpr int RG = SM ? 16 : (sizeof(R) == 4 ? 64 : 32); // RHS per CTA
   static constexpr int NHG = RG / RPT;                // RHS groups
   static constexpr int NCONS = NRG * NHG;             // consumer threads
   static constexpr int LDR = RG + 2;                  // row stride of the [W][RG] exchange arrays
@@ -202,9 +205,9 @@ __device__ __forceinline__ bool consumer_barrier_and(int nthreads, bool v) {
 }
 
 // Shared-memory bytes of phases 1 and 3.
-template <typename R, int W>
+template <typename R, int W, bool SM>
 size_t tile_smem(int d_out, bool p3) {
-  using TL = Tile13<R, W>;
+  using TL = Tile13<R, W, SM>;
   const size_t pb = round128((size_t)payload_elems(W, d_out) * sizeof(cplx<R>));
   const size_t vb = round128((size_t)W * TL::LDR * sizeof(cplx<R>));  // one W x RG array (padded)
   // phase 1: ring of payloads, Y and g double buffers
@@ -216,10 +219,10 @@ size_t tile_smem(int d_out, bool p3) {
 //   y_j = g_j - C_{j-1} z_{j-1},  z_j = G_j y_j  (z_j stored for phase 3),
 // the left-spike sum sum_j W_j^t g_j, and the separator term C_r z_r - g(s).
 // Thread (rg, hg) owns rows rg + NRG*i (i < ROWS) and RHS 2hg, 2hg+1 of the group.
-template <typename R, int W>
-__global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase1_kernel(SweepArgs a) {
+template <typename R, int W, bool SM>
+__global__ void __launch_bounds__(Tile13<R, W, SM>::NCONS + 32) phase1_kernel(SweepArgs a) {
   using C = cplx<R>;
-  using TL = Tile13<R, W>;
+  using TL = Tile13<R, W, SM>;
   constexpr int ROWS = TL::ROWS, NRG = TL::NRG, RPT = TL::RPT, RG = TL::RG, NCONS = TL::NCONS, LDR = TL::LDR;
   constexpr int LDP = W + 2;
   static_assert(RPT == 2, "tiles carry two right-hand sides");
@@ -731,10 +734,10 @@ __global__ void __launch_bounds__(2 * npart<R>() * wpc_max<R>() * 32 + 64) phase
 // correction -W_j beta, beta = C_{l-1} x_{left separator}.  Each ring stage
 // brings the column payload and the CTA's tile of the stored z_j.  Thread
 // (rg, hg) owns rows rg + NRG*i and RHS 2hg, 2hg+1 of the group.
-template <typename R, int W>
-__global__ void __launch_bounds__(Tile13<R, W>::NCONS + 32) phase3_kernel(SweepArgs a) {
+template <typename R, int W, bool SM>
+__global__ void __launch_bounds__(Tile13<R, W, SM>::NCONS + 32) phase3_kernel(SweepArgs a) {
   using C = cplx<R>;
-  using TL = Tile13<R, W>;
+  using TL = Tile13<R, W, SM>;
   constexpr int ROWS = TL::ROWS, NRG = TL::NRG, RPT = TL::RPT, RG = TL::RG, NCONS = TL::NCONS, LDR = TL::LDR;
   constexpr int LDP = W + 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -949,8 +952,10 @@ template <typename R, int W>
 void set_attrs_w() {
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(phase1_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    cudaFuncSetAttribute(phase3_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(phase1_kernel<R, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(phase3_kernel<R, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(phase1_kernel<R, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(phase3_kernel<R, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(phase2_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   });
 }
@@ -960,28 +965,35 @@ void set_attrs() {
   set_attrs_w<R, 8>(); set_attrs_w<R, 12>(); set_attrs_w<R, 16>(); set_attrs_w<R, 24>(); set_attrs_w<R, 32>();
 }
 
-template <typename R, int W>
-int run_stage_w(const Plan& p, SweepArgs a, cudaStream_t s) {
-  using TL = Tile13<R, W>;
+// One stage: chunk tiles of 16 RHS when the stage has at most 16, else the
+// full tile.
+template <typename R, int W, bool SM>
+int run_stage_t(const Plan& p, SweepArgs a, cudaStream_t s) {
+  using TL = Tile13<R, W, SM>;
   const int dmax = std::max(a.blk[0].d_out, a.nfront > 1 ? a.blk[1].d_out : 0);
-  const size_t sm1 = tile_smem<R, W>(dmax, false);
-  const size_t sm3 = tile_smem<R, W>(dmax, true);
+  const size_t sm1 = tile_smem<R, W, SM>(dmax, false);
+  const size_t sm3 = tile_smem<R, W, SM>(dmax, true);
   set_attrs_w<R, W>();
   const int wpc = p.opt.sep_rhs_per_cta > 0 ? std::min(p.opt.sep_rhs_per_cta, wpc_max<R>())
                                             : phase2_wpc(a.R, a.nfront, wpc_max<R>());
   if (sm1 > 220 * 1024 || sm3 > 220 * 1024 || phase2_smem<R, W>(a.P - 1, wpc) > 220 * 1024) return HS_EUNSUPPORTED;
   dim3 g13(a.P, (a.R + TL::RG - 1) / TL::RG, a.nfront);
   note_launch();
-  phase1_kernel<R, W><<<g13, TL::NCONS + 32, sm1, s>>>(a);
+  phase1_kernel<R, W, SM><<<g13, TL::NCONS + 32, sm1, s>>>(a);
   if (a.P > 1) {
     dim3 g2(1, (a.R + wpc - 1) / wpc, a.nfront);
     note_launch();
     phase2_kernel<R, W><<<g2, 2 * npart<R>() * wpc * 32 + 64, phase2_smem<R, W>(a.P - 1, wpc), s>>>(a);
   }
   note_launch();
-  phase3_kernel<R, W><<<g13, TL::NCONS + 32, sm3, s>>>(a);
+  phase3_kernel<R, W, SM><<<g13, TL::NCONS + 32, sm3, s>>>(a);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HS_OK : cuda_status(e);
+}
+
+template <typename R, int W>
+int run_stage_w(const Plan& p, SweepArgs a, cudaStream_t s) {
+  return a.R <= Tile13<R, W, true>::RG ? run_stage_t<R, W, true>(p, a, s) : run_stage_t<R, W, false>(p, a, s);
 }
 
 template <typename R>
