@@ -216,15 +216,23 @@ __device__ __forceinline__ bool consumer_barrier_and(int nthreads, bool v) {
   return r != 0;
 }
 
+// Depth of phase 3's staging of the previous u values (backward stages, full
+// tile): each thread copies its own output entries OD - 1 columns ahead with
+// cp.async (n = 2047, 64 RHS: 29.5 -> 29.1 ms per application; depths 4 and 5
+// the same).  The 16-RHS tile keeps register prefetches (staged: 0.6-0.75 ms
+// slower at 1-16 RHS).
+constexpr int OD = 3;
+
 // Shared-memory bytes of phases 1 and 3.
 template <typename R, int W, bool SM>
 size_t tile_smem(int d_out, bool p3) {
   using TL = Tile13<R, W, SM>;
   const size_t pb = round128((size_t)payload_elems(W, d_out) * sizeof(cplx<R>));
   const size_t vb = round128((size_t)W * TL::LDR * sizeof(cplx<R>));  // one W x RG array (padded)
+  const size_t ob = SM ? 0 : round128((size_t)OD * d_out * TL::LDR * sizeof(cplx<R>));   // [OD][d_out][LDR]
   // phase 1: ring of payloads, Y and g double buffers
-  // phase 3: ring of (payload + z tile), tv double buffer, beta
-  return p3 ? 256 + S13 * (pb + vb) + 3 * vb : 256 + S13 * pb + 4 * vb;
+  // phase 3: ring of (payload + z tile), tv double buffer, beta, old-u staging
+  return p3 ? 256 + S13 * (pb + vb) + 3 * vb + ob : 256 + S13 * pb + 4 * vb;
 }
 
 // Forward elimination over the chunk's interior columns:
@@ -778,6 +786,7 @@ __global__ void __launch_bounds__(Tile13<R, W, SM>::NCONS + 32 * P13) phase3_ker
   const size_t sstride = pstride + vb;
   C* tvbuf = reinterpret_cast<C*>(smem_raw + 256 + S13 * sstride);            // [2][W][LDR]
   C* beta = reinterpret_cast<C*>(smem_raw + 256 + S13 * sstride + 2 * vb);     // [W][LDR]
+  C* olds = reinterpret_cast<C*>(smem_raw + 256 + S13 * sstride + 3 * vb);     // [OD][d_out][LDR]
   const C* fac = reinterpret_cast<const C*>(a.fac) + d.fac_off;
   const int tid = threadIdx.x;
   const int rbase = blockIdx.y * RG;
@@ -859,6 +868,40 @@ __global__ void __launch_bounds__(Tile13<R, W, SM>::NCONS + 32 * P13) phase3_ker
   bool isout[ROWS];
 #pragma unroll
   for (int i = 0; i < ROWS; ++i) isout[i] = (rg + NRG * i >= d.out_off) && (rg + NRG * i < d.out_off + d.d_out);
+  // backward stages subtract from the previous u: each thread copies its own
+  // output entries of column rgt - t into staging slot t % OD (one commit
+  // group per column, empty when there is nothing to copy)
+  auto old_slot = [&](int t, int i) {
+    return olds + ((size_t)(t % OD) * d.d_out + (rg + NRG * i - d.out_off)) * LDR + c0;
+  };
+  auto issue_old = [&](int t) {
+    if (t < ncol) {
+      const int j = rgt - t;
+#pragma unroll
+      for (int i = 0; i < ROWS; ++i)
+        if (isout[i]) {
+          C* dst = old_slot(t, i);
+#pragma unroll
+          for (int q = 0; q < RPT; ++q) {
+            const C* src = u + (long long)(d.wlo + rg + NRG * i - 1) * rs + (long long)j * a.R + rr[q];
+            if constexpr (sizeof(R) == 4) cp_async8(dst + q, src);
+            else cp_async16(dst + q, src);
+          }
+        }
+    }
+    cp_async_commit();
+  };
+  auto read_old = [&](int t, C (&uo)[RPT][ROWS]) {
+    cp_async_wait<OD - 1>();      // column t's group has landed
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i)
+      if (isout[i]) {
+        const C* src = old_slot(t, i);
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) uo[q][i] = src[q];
+      }
+  };
+  // register prefetch of the same entries (16-RHS tile)
   auto load_old = [&](C (&o)[RPT][ROWS], int j) {
 #pragma unroll
     for (int q = 0; q < RPT; ++q)
@@ -942,17 +985,32 @@ __global__ void __launch_bounds__(Tile13<R, W, SM>::NCONS + 32 * P13) phase3_ker
       }
     }
   };
-  C o0[RPT][ROWS], o1[RPT][ROWS];
-  load_old(o0, rgt);
-  if (ncol > 1) load_old(o1, rgt - 1);
-  for (int t = 0; t < ncol; t += 2) {
-    step(t, o0);
-    if (!ok) break;
-    if (t + 2 < ncol) load_old(o0, rgt - t - 2);
-    if (t + 1 < ncol) {
-      step(t + 1, o1);
+  if constexpr (!SM) {
+    if (bwd)
+      for (int t = 0; t < OD - 1; ++t) issue_old(t);
+    for (int t = 0; t < ncol; ++t) {
+      C uo[RPT][ROWS] = {};
+      if (bwd) {
+        issue_old(t + OD - 1);
+        read_old(t, uo);
+      }
+      step(t, uo);
       if (!ok) break;
-      if (t + 3 < ncol) load_old(o1, rgt - t - 3);
+    }
+    if (bwd) cp_async_wait_all();
+  } else {
+    C o0[RPT][ROWS], o1[RPT][ROWS];
+    load_old(o0, rgt);
+    if (ncol > 1) load_old(o1, rgt - 1);
+    for (int t = 0; t < ncol; t += 2) {
+      step(t, o0);
+      if (!ok) break;
+      if (t + 2 < ncol) load_old(o0, rgt - t - 2);
+      if (t + 1 < ncol) {
+        step(t + 1, o1);
+        if (!ok) break;
+        if (t + 3 < ncol) load_old(o1, rgt - t - 3);
+      }
     }
   }
   if (!ok) {
