@@ -37,11 +37,11 @@ sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) of one sweep application, from an ncu capture of
 # the phase 1/2/3 kernels of one stage at n = 1023 (both fronts;
-# dram__bytes_read.sum + dram__bytes_write.sum = 74.4 MB), scaled by the
-# columns per stage to n = 2047 (148.9 MB) and by the 173 stage executions of
+# dram__bytes_read.sum + dram__bytes_write.sum = 74.29 MB), scaled by the
+# columns per stage to n = 2047 (148.6 MB) and by the 173 stage executions of
 # the plan.  Keyed by (n, layers per step, RHS, factor precision); None
 # elsewhere or when the kernels changed since the capture.
-SWEEP_TRAFFIC = {(2047, 12, 64, 64): 74.38e6 * (2047.0 / 1023.0) * 173}
+SWEEP_TRAFFIC = {(2047, 12, 64, 64): 74.29e6 * (2047.0 / 1023.0) * 173}
 
 METRIC = "GMRES time-to-1e-6 & sweep applies/s (2D n=2047, 64 RHS), % HBM roofline"
 UNIT = "rhs_solved_per_s"
