@@ -77,12 +77,58 @@ __device__ __forceinline__ void df_fma_f(df& acc, df x, float y) {
   acc = fast_two_sum(s.h, s.l);
 }
 
-// conversions that use the FP64 pipe (boundaries and small vectors only)
-__device__ __forceinline__ df df_from_double(double x) {
+// Conversions between FP64 and double-float.  Bulk vectors cross this
+// boundary (the ABI's complex128 right-hand sides and solutions, the FP64
+// right-hand side of the true residual), so both directions work on the
+// IEEE-754 bit fields with integer and FP32 instructions and leave at most one
+// FP64 operation per value; GB300's FP64 pipe otherwise bounds those passes.
+//
+// double -> df: h takes the sign, the exponent (rebiased 1023 -> 127) and the
+// top 23 of the 52 stored mantissa bits; the 29 remaining bits, scaled by
+// 2^(E-52), become l (an integer-to-float conversion, rounded to 24 bits, and
+// a multiplication by a power of two); FastTwoSum then restores |l| <=
+// ulp(h)/2.  Relative error about 2^-48.  Zero is exact; values outside the
+// normal FP32 range, infinities and NaNs take the FP64 route.
+// (kept out of line so that the rare FP64 route is a branch, not predicated
+// FP64 instructions issued for every value)
+static __device__ __noinline__ df df_from_double_fp64(double x) {
   const float h = __double2float_rn(x);
   return df{h, __double2float_rn(x - (double)h)};
 }
-__device__ __forceinline__ double df_to_double(df a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ df df_from_double(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7FF);
+  const unsigned sgn = (unsigned)(u >> 32) & 0x80000000u;
+  const int fe = e - 896;                       // FP32 exponent field of h
+  if (fe >= 1 && fe <= 254) {
+    const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+    const float h = __uint_as_float(sgn | ((unsigned)fe << 23) | (unsigned)(m >> 29));
+    float l = 0.f;
+    const int pe = e - 948;                     // FP32 exponent field of 2^(E-52)
+    if (pe >= 1) {
+      const float r = __uint2float_rn((unsigned)(m & 0x1FFFFFFFull));
+      l = __fmul_rn(r, __uint_as_float((unsigned)pe << 23));
+      if (sgn) l = -l;
+    }
+    return fast_two_sum(h, l);
+  }
+  if (e == 0) return df{__uint_as_float(sgn), 0.f};   // zero (and FP64 subnormals, far below FP32's range)
+  return df_from_double_fp64(x);
+}
+static __device__ __noinline__ double f2d_fp64(float f) { return (double)f; }
+// float -> double by its bit fields (normal numbers and zero; the rest by
+// the conversion instruction), then one FP64 addition.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned ef = (b >> 23) & 0xFF;
+  const unsigned long long sg = (unsigned long long)(b & 0x80000000u) << 32;
+  if (ef >= 1 && ef <= 254)
+    return __longlong_as_double((long long)(sg | ((unsigned long long)(ef + 896) << 52) |
+                                            ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+  if ((b & 0x7FFFFFFFu) == 0) return __longlong_as_double((long long)sg);
+  return f2d_fp64(f);
+}
+__device__ __forceinline__ double df_to_double(df a) { return f2d_bits(a.h) + f2d_bits(a.l); }
 __device__ __forceinline__ cdf cdf_from_c128(c128 z) { return cdf{df_from_double(z.re), df_from_double(z.im)}; }
 __device__ __forceinline__ c128 cdf_to_c128(cdf z) { return c128{df_to_double(z.re), df_to_double(z.im)}; }
 

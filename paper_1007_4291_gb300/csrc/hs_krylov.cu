@@ -337,39 +337,58 @@ __global__ void __launch_bounds__(KT) xcorrect_kernel(const c64* __restrict__ Z,
 }
 
 // Layout conversion ABI [rhs][point] (complex128) <-> solver [point][rhs] (V).
+// Each CTA moves 32 x 32 tiles (points x RHS) through shared memory, looping
+// over point tiles; each thread fetches its four entries of the next tile
+// before it writes out the current one, so loads stay in flight across the
+// tile's barriers.
 template <typename AR, bool TO_INTERNAL>
 __global__ void relayout_v_kernel(const void* __restrict__ srcv, void* __restrict__ dstv, long long npts, int R) {
   using V = typename AR::V;
   __shared__ V tile[32][33];
-  const long long p0 = (long long)blockIdx.x * 32;
   const int r0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  for (int yy = ty; yy < 32; yy += 8) {
-    if (TO_INTERNAL) {
-      const c128* src = reinterpret_cast<const c128*>(srcv);
-      const long long pt = p0 + tx;
-      const int r = r0 + yy;
-      if (pt < npts && r < R) tile[yy][tx] = AR::from_c128(src[(long long)r * npts + pt]);
-    } else {
-      const V* src = reinterpret_cast<const V*>(srcv);
-      const long long pt = p0 + yy;
-      const int r = r0 + tx;
-      if (pt < npts && r < R) tile[yy][tx] = src[pt * R + r];
+  const long long step = (long long)gridDim.x * 32;
+  V pre[4];
+  auto fetch = [&](long long p0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int yy = ty + 8 * q;
+      if (TO_INTERNAL) {
+        const c128* src = reinterpret_cast<const c128*>(srcv);
+        const long long pt = p0 + tx;
+        const int r = r0 + yy;
+        if (pt < npts && r < R) pre[q] = AR::from_c128(src[(long long)r * npts + pt]);
+      } else {
+        const V* src = reinterpret_cast<const V*>(srcv);
+        const long long pt = p0 + yy;
+        const int r = r0 + tx;
+        if (pt < npts && r < R) pre[q] = src[pt * R + r];
+      }
     }
-  }
-  __syncthreads();
-  for (int yy = ty; yy < 32; yy += 8) {
-    if (TO_INTERNAL) {
-      V* dst = reinterpret_cast<V*>(dstv);
-      const long long pt = p0 + yy;
-      const int r = r0 + tx;
-      if (pt < npts && r < R) dst[pt * R + r] = tile[tx][yy];
-    } else {
-      c128* dst = reinterpret_cast<c128*>(dstv);
-      const long long pt = p0 + tx;
-      const int r = r0 + yy;
-      if (pt < npts && r < R) dst[(long long)r * npts + pt] = AR::out_c128(tile[tx][yy]);
+  };
+  long long p0 = (long long)blockIdx.x * 32;
+  if (p0 < npts) fetch(p0);
+  for (; p0 < npts; p0 += step) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tile[ty + 8 * q][tx] = pre[q];
+    __syncthreads();
+    if (p0 + step < npts) fetch(p0 + step);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int yy = ty + 8 * q;
+      if (TO_INTERNAL) {
+        V* dst = reinterpret_cast<V*>(dstv);
+        const long long pt = p0 + yy;
+        const int r = r0 + tx;
+        if (pt < npts && r < R) dst[pt * R + r] = tile[tx][yy];
+      } else {
+        c128* dst = reinterpret_cast<c128*>(dstv);
+        const long long pt = p0 + tx;
+        const int r = r0 + yy;
+        if (pt < npts && r < R) dst[(long long)r * npts + pt] = AR::out_c128(tile[tx][yy]);
+      }
     }
+    __syncthreads();
   }
 }
 
@@ -561,10 +580,16 @@ struct Solver {
   void dots(const V* Vb, int nv, const V* v) {
     const dim3 g = grid();
     note_launch();
-    if (nv <= 8) dots_kernel<AR, 8><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
+    // the smallest instantiation that holds nv vectors: the per-thread
+    // accumulators and loads of the larger ones cost registers, and with
+    // them resident warps (DF64 with room for 8 vectors: 165 registers, one
+    // CTA per SM, 1.3 TB/s for a norm)
+    if (nv <= 1) dots_kernel<AR, 1><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
+    else if (nv <= 4) dots_kernel<AR, 4><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
+    else if (nv <= 8) dots_kernel<AR, 8><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
     else if (nv <= 16) dots_kernel<AR, 16><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
     else dots_kernel<AR, 32><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
-    const int mj = (nv <= 8) ? 8 : (nv <= 16) ? 16 : 32;
+    const int mj = (nv <= 1) ? 1 : (nv <= 4) ? 4 : (nv <= 8) ? 8 : (nv <= 16) ? 16 : 32;
     note_launch();
     reduce_parts_kernel<<<((nv + 1) * R + 255) / 256, 256, 0, s>>>(w.part, nctas, mj + 1, nv + 1, R, w.h);
   }
@@ -572,7 +597,8 @@ struct Solver {
   void update(const V* Vb, int nv, V* v, int slot, const double* iscale = nullptr, V* vcopy = nullptr) {
     const dim3 g = grid();
     note_launch();
-    if (nv <= 8) update_kernel<AR, 8><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part, iscale, vcopy);
+    if (nv <= 4) update_kernel<AR, 4><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part, iscale, vcopy);
+    else if (nv <= 8) update_kernel<AR, 8><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part, iscale, vcopy);
     else if (nv <= 16) update_kernel<AR, 16><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part, iscale, vcopy);
     else update_kernel<AR, 32><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part, iscale, vcopy);
     note_launch();
@@ -580,9 +606,9 @@ struct Solver {
   }
   void norm2(const V* v, int slot) {
     note_launch();
-    dots_kernel<AR, 8><<<grid(), KT, 0, s>>>(nullptr, vs, 0, v, npts, R, w.part);
+    dots_kernel<AR, 1><<<grid(), KT, 0, s>>>(nullptr, vs, 0, v, npts, R, w.part);
     note_launch();
-    reduce_parts_kernel<<<(R + 255) / 256, 256, 0, s>>>(w.part, nctas, 9, 1, R, w.h + (long long)slot * R);
+    reduce_parts_kernel<<<(R + 255) / 256, 256, 0, s>>>(w.part, nctas, 2, 1, R, w.h + (long long)slot * R);
   }
   // dst = src * f[r]; the host factors are copied synchronously (tiny)
   void scale(const V* src, const std::vector<double>& f, V* dst) {
@@ -641,7 +667,8 @@ struct Solver {
     to_c64_kernel<AR><<<sm_count() * 8, 256, 0, s>>>(v, z, vs);
   }
   void relayout(const void* src, void* dst, bool to_internal) {
-    dim3 gr((unsigned)((npts + 31) / 32), (R + 31) / 32);
+    const long long tiles = (npts + 31) / 32;
+    dim3 gr((unsigned)std::min<long long>(tiles, (long long)sm_count() * 8), (R + 31) / 32);
     note_launch();
     if (to_internal) relayout_v_kernel<AR, true><<<gr, dim3(32, 8), 0, s>>>(src, dst, npts, R);
     else relayout_v_kernel<AR, false><<<gr, dim3(32, 8), 0, s>>>(src, dst, npts, R);
