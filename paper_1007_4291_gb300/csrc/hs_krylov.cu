@@ -410,7 +410,9 @@ __device__ __forceinline__ cdf ld_x(const void* x, long long k) {
 }
 
 // One warp per grid point and 32 consecutive RHS (coordinates and
-// coefficients warp-uniform, neighbour rows contiguous).
+// coefficients warp-uniform, neighbour rows contiguous).  Each warp takes two
+// points per iteration and issues all loads of both before it computes, so
+// that twice as many loads are in flight.
 template <bool XDF, bool RESID>
 __global__ void __launch_bounds__(256) matvec_df_kernel(const void* __restrict__ x, cdf* __restrict__ y,
                                                         const cdf* __restrict__ f, DfTabs t, int n, int R) {
@@ -420,34 +422,60 @@ __global__ void __launch_bounds__(256) matvec_df_kernel(const void* __restrict__
   const int n2 = n * n;
   const cdf zero{df{0.f, 0.f}, df{0.f, 0.f}};
   const long long sx = R, sy = (long long)n * R;
-  for (int pt = blockIdx.x * 8 + warp; pt < n2; pt += gridDim.x * 8) {
-    const int j = pt / n, i = pt - j * n;
+  struct Pt {
+    cdf xc, xe, xw, xn, xs, fv;
+    df m0;
+    int i, j;
+    bool pml;
+  };
+  auto load = [&](int pt, Pt& q) {
+    q.j = pt / n;
+    q.i = pt - q.j * n;
     const long long e = (long long)pt * R + r;
-    const cdf xc = ld_x<XDF>(x, e);
-    const cdf xe = (i + 1 < n) ? ld_x<XDF>(x, e + sx) : zero;
-    const cdf xw = (i > 0) ? ld_x<XDF>(x, e - sx) : zero;
-    const cdf xn = (j + 1 < n) ? ld_x<XDF>(x, e + sy) : zero;
-    const cdf xs = (j > 0) ? ld_x<XDF>(x, e - sy) : zero;
-    const df m0 = t.m0[pt];
+    q.xc = ld_x<XDF>(x, e);
+    q.xe = (q.i + 1 < n) ? ld_x<XDF>(x, e + sx) : zero;
+    q.xw = (q.i > 0) ? ld_x<XDF>(x, e - sx) : zero;
+    q.xn = (q.j + 1 < n) ? ld_x<XDF>(x, e + sy) : zero;
+    q.xs = (q.j > 0) ? ld_x<XDF>(x, e - sy) : zero;
+    q.fv = RESID ? f[e] : zero;
+    q.m0 = t.m0[pt];
+    q.pml = t.pml1[q.i + 1] || t.pml2[q.j + 1];
+  };
+  auto apply = [&](int pt, const Pt& q) {
     cdf acc;
-    if (!t.pml1[i + 1] && !t.pml2[j + 1]) {
-      const df dg = df_add(m0, df{-4.f * t.ih2, 0.f});
-      const cdf s4 = cdf_add(cdf_add(xe, xw), cdf_add(xn, xs));
-      acc.re = df_add(df_mul_f(s4.re, t.ih2), df_mul(dg, xc.re));
-      acc.im = df_add(df_mul_f(s4.im, t.ih2), df_mul(dg, xc.im));
+    if (!q.pml) {
+      const df dg = df_add(q.m0, df{-4.f * t.ih2, 0.f});
+      const cdf s4 = cdf_add(cdf_add(q.xe, q.xw), cdf_add(q.xn, q.xs));
+      acc.re = df_add(df_mul_f(s4.re, t.ih2), df_mul(dg, q.xc.re));
+      acc.im = df_add(df_mul_f(s4.im, t.ih2), df_mul(dg, q.xc.im));
     } else {
+      const int i = q.i, j = q.j;
       const cdf is1 = t.inv_s1[i + 1], is2 = t.inv_s2[j + 1];
       const cdf E = cdf_mul(t.a1[i + 1], is2), Wc = cdf_mul(t.a1[i], is2);
       const cdf N = cdf_mul(t.a2[j + 1], is1), S = cdf_mul(t.a2[j], is1);
       const cdf ss = cdf_mul(is1, is2);
-      const cdf D = cdf_sub(cdf{df_mul(ss.re, m0), df_mul(ss.im, m0)}, cdf_add(cdf_add(E, Wc), cdf_add(N, S)));
-      acc = cdf_mul(D, xc);
-      acc = cdf_add(acc, cdf_mul(E, xe));
-      acc = cdf_add(acc, cdf_mul(Wc, xw));
-      acc = cdf_add(acc, cdf_mul(N, xn));
-      acc = cdf_add(acc, cdf_mul(S, xs));
+      const cdf D = cdf_sub(cdf{df_mul(ss.re, q.m0), df_mul(ss.im, q.m0)}, cdf_add(cdf_add(E, Wc), cdf_add(N, S)));
+      acc = cdf_mul(D, q.xc);
+      acc = cdf_add(acc, cdf_mul(E, q.xe));
+      acc = cdf_add(acc, cdf_mul(Wc, q.xw));
+      acc = cdf_add(acc, cdf_mul(N, q.xn));
+      acc = cdf_add(acc, cdf_mul(S, q.xs));
     }
-    y[e] = RESID ? cdf_sub(f[e], acc) : acc;
+    y[(long long)pt * R + r] = RESID ? cdf_sub(q.fv, acc) : acc;
+  };
+  const int stride = gridDim.x * 8;
+  int pt = blockIdx.x * 8 + warp;
+  for (; pt + stride < n2; pt += 2 * stride) {
+    Pt a, b;
+    load(pt, a);
+    load(pt + stride, b);
+    apply(pt, a);
+    apply(pt + stride, b);
+  }
+  if (pt < n2) {
+    Pt a;
+    load(pt, a);
+    apply(pt, a);
   }
 }
 
