@@ -694,8 +694,12 @@ def run_ours(args):
     lib = hs.load()
     wl = workload(args, rank)
     n, R = wl["n"], args.nrhs
+    # async_setup: hs_setup returns once the factorisation is queued; the solve
+    # on the same stream follows it, and the end-to-end step uploads the
+    # right-hand sides while the setup kernels run
     opt = hs.hs_default_options(alpha=wl["alpha"], pml_C=wl["C"], layers_per_step=args.dl, factor_prec=args.prec,
-                                chunk=args.chunk, max_nrhs=R, restart=args.restart, krylov_basis=args.krylov_basis)
+                                chunk=args.chunk, max_nrhs=R, restart=args.restart, krylov_basis=args.krylov_basis,
+                                async_setup=1)
     stream = torch.cuda.current_stream()
     c_host = np.ascontiguousarray(wl["c"].ravel())
     f_dev = torch.from_numpy(wl["f"]).to("cuda")
@@ -743,10 +747,12 @@ def run_ours(args):
         copy_stream = torch.cuda.Stream()
 
         def step_e2e():
-            # the right-hand sides upload on a side stream while the setup runs
+            # the setup is queued first (its own small table uploads go ahead of
+            # the 4.3 GB right-hand sides on the copy engine), then the right-hand
+            # sides upload on a side stream while the setup kernels run
+            plan = hs.hs_setup(c_host, wl["omega"], n, 2, wl["bp"], wl["b"], opt, stream)
             with torch.cuda.stream(copy_stream):
                 f_dev.copy_(f_host, non_blocking=True)
-            plan = hs.hs_setup(c_host, wl["omega"], n, 2, wl["bp"], wl["b"], opt, stream)
             u_dev.zero_()
             stream.wait_stream(copy_stream)
             code, info = hs.hs_solve(plan, f_dev, u_dev, R, args.tol, 400, stream)

@@ -101,6 +101,14 @@ typedef struct {
                             the grid boundary is cut there and keeps the operator's own profile
                             (the exact Schur inverse).  2D only; windows must stay <= 32 rows.
                                                                                            default 0 */
+  int async_setup;       /* 1 (2D hs_setup only): hs_setup returns as soon as the factorisation is
+                            queued on its stream instead of waiting for it, so that the caller can
+                            overlap its own work (e.g. uploading right-hand sides) with the setup
+                            kernels.  Every later call on the plan orders itself after the setup
+                            on its own stream; a zero pivot is then reported by the next call that
+                            synchronises (hs_sync, hs_solve, hs_last_device_status) instead of by
+                            hs_setup.  The velocities are copied before hs_setup returns either
+                            way.  No counterpart in the paper.                          default 0 */
 } hs_options;
 
 typedef struct hs_plan hs_plan;
@@ -135,7 +143,8 @@ int hs_default_options(hs_options* opt);
  * pml_width         b_p: boundary PML width in grid points, eta = b_p h (Eq. sigma).
  * moving_pml_width  b: moving PML width in grid points (Eq. helma), 1 <= b <= b_p + 1.
  * opt      NULL for defaults.
- * stream   stream for the setup kernels; the call synchronises it before returning.
+ * stream   stream for the setup kernels; the call synchronises it before returning
+ *          (unless opt->async_setup, see there).
  * out      receives the plan.
  *
  * Every subproblem H_m (the front F, the end E, every d-layer block of both

@@ -93,6 +93,7 @@ extern "C" int hs_apply_batched(int nprob, hs_plan* const* plans, const void* co
   }
   key.push_back(dtype);
   cudaStream_t s = (cudaStream_t)stream;
+  for (Plan* q : ps) plan_wait(*q, s);
   std::lock_guard<std::mutex> lock(g_batch_mutex);
   for (size_t i = 0; i < g_batch.size(); ++i) {
     if (g_batch[i].key == key) {

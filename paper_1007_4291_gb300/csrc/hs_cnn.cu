@@ -699,6 +699,7 @@ extern "C" int hs_cnn_train_step_residual(hs_cnn* net, hs_plan* plan, const void
   const int n = p.n, n2 = n * n, R = nrhs;
   HS_TRY_INT(c.reserve_train(R, n));
   cudaStream_t s = (cudaStream_t)stream;
+  plan_wait(p, s);
   c64* cb = static_cast<c64*>(c.rbuf);
   c64* ab = cb + (size_t)R * n2;
   c64* db = ab + (size_t)R * n2;

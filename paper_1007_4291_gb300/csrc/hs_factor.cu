@@ -481,7 +481,7 @@ size_t factor_smem(int W) {
 }
 
 template <typename R>
-int launch_setup_t(const std::vector<Plan*>& ps, cudaStream_t s) {
+int launch_setup_t(const std::vector<Plan*>& ps, cudaStream_t s, bool async) {
   std::vector<FactorArgs> args;
   std::vector<FactorItem> items, reduced;
   int Wmax = 8;
@@ -508,8 +508,10 @@ int launch_setup_t(const std::vector<Plan*>& ps, cudaStream_t s) {
   std::stable_sort(reduced.begin(), reduced.end(), wider);
   const size_t abytes = ((args.size() * sizeof(FactorArgs) + 255) / 256) * 256;
   const size_t ibytes = items.size() * sizeof(FactorItem), rbytes = reduced.size() * sizeof(FactorItem);
+  // the launch arguments live in stream-ordered memory, released on the
+  // stream after the kernels (no device-wide synchronisation)
   char* buf = nullptr;
-  HS_CUDA_TRY(cudaMalloc(&buf, abytes + ibytes + rbytes + 16));
+  HS_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&buf), abytes + ibytes + rbytes + 16, s));
   FactorArgs* d_args = reinterpret_cast<FactorArgs*>(buf);
   FactorItem* d_items = reinterpret_cast<FactorItem*>(buf + abytes);
   FactorItem* d_red = reinterpret_cast<FactorItem*>(buf + abytes + ibytes);
@@ -535,18 +537,19 @@ int launch_setup_t(const std::vector<Plan*>& ps, cudaStream_t s) {
     factor_reduced_kernel<R><<<g2, 32, smem, s>>>(d_args, d_red, (int)reduced.size());
     e = cudaGetLastError();
   }
-  cudaError_t e2 = cudaStreamSynchronize(s);
-  cudaFree(buf);
+  cudaFreeAsync(buf, s);
   if (e != cudaSuccess) return cuda_status(e);
+  if (async) return HS_OK;
+  cudaError_t e2 = cudaStreamSynchronize(s);
   if (e2 != cudaSuccess) return cuda_status(e2);
   return HS_OK;
 }
 
 }  // namespace
 
-int launch_setup(const std::vector<Plan*>& ps, cudaStream_t s) {
+int launch_setup(const std::vector<Plan*>& ps, cudaStream_t s, bool async) {
   if (ps.empty()) return HS_OK;
-  return (ps[0]->prec == HS_C64) ? launch_setup_t<float>(ps, s) : launch_setup_t<double>(ps, s);
+  return (ps[0]->prec == HS_C64) ? launch_setup_t<float>(ps, s, async) : launch_setup_t<double>(ps, s, async);
 }
 
 }  // namespace hs

@@ -77,6 +77,7 @@ struct Plan {
   double omega = 0, alpha = 0, C = 0, Cm = 0, h = 0;   // C boundary PML, Cm moving PMLs
   int prec = HS_C64;  // factor precision
   int device = 0;     // CUDA device current at setup (owns every device buffer of the plan)
+  cudaEvent_t ready = nullptr;   // asynchronous setup: recorded after the setup's last kernel
   int L = 32, P = 1;  // x1 chunk length and chunk count
   int max_nrhs = 64;
   hs_options opt{};
@@ -159,7 +160,15 @@ int capture_graph(cudaStream_t cap, F&& body, cudaGraphExec_t* exec, long long* 
 // launchers (defined in the .cu files)
 // factor every block of every plan of `ps` (same factor precision): one
 // launch over all chunks, one over all reduced systems; synchronises `s`
-int launch_setup(const std::vector<Plan*>& ps, cudaStream_t s);
+int launch_setup(const std::vector<Plan*>& ps, cudaStream_t s, bool async = false);
+// Order work on stream s after an asynchronous setup of plan p (no-op once
+// the plan was set up synchronously).
+inline void plan_wait(const Plan& p, cudaStream_t s) {
+  if (p.ready) cudaStreamWaitEvent(s, p.ready, 0);
+}
+inline void plan_wait_host(const Plan& p) {
+  if (p.ready) cudaEventSynchronize(p.ready);
+}
 // u <- M_alpha u on p.d_u.  graph: replay (or capture on first use) the
 // stage chain as one CUDA graph keyed by nrhs and the scratch pointers.
 int sweep_internal(Plan& p, int nrhs, cudaStream_t s, bool graph = false);

@@ -1158,6 +1158,7 @@ extern "C" int hs_solve(hs_plan* plan, const void* f, void* u, int nrhs, double 
   Plan& p = *reinterpret_cast<Plan*>(plan);
   if (nrhs < 1 || nrhs > p.max_nrhs) return HS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  plan_wait(p, s);
   // 3D plans keep the Krylov vectors in FP64 (the double-float kernels are 2D)
   if (p.prec == HS_C64 && p.dim == 2 && p.opt.krylov_basis == 1 && !p.cnn)
     return solve_refine(p, f, u, nrhs, tol, maxit, info, s);

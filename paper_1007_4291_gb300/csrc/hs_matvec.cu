@@ -318,6 +318,7 @@ extern "C" int hs_matvec(hs_plan* plan, const void* x, void* y, int nrhs, int dt
   if (!plan || !x || !y || x == y) return HS_EINVAL;
   Plan& p = *reinterpret_cast<Plan*>(plan);
   if (nrhs < 1 || (dtype != HS_C64 && dtype != HS_C128)) return HS_EINVAL;
+  plan_wait(p, (cudaStream_t)stream);
   if (p.dim == 3) return matvec3_abi(p, x, y, nrhs, dtype, (cudaStream_t)stream);
   return matvec_abi(p, x, y, nrhs, dtype, (cudaStream_t)stream);
 }

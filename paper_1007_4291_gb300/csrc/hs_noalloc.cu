@@ -74,6 +74,7 @@ extern "C" int hs_apply_noalloc(hs_plan* plan, const void* r, void* z, int nrhs,
   void* base = nullptr;
   int st = scratch_address(dev, &base);
   if (st != HS_OK) return st;
+  plan_wait(p, (cudaStream_t)stream);
   char* q = static_cast<char*>(base);
   SweepWork w{};
   w.u = q; q += bu;

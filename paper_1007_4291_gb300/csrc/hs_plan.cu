@@ -159,6 +159,7 @@ extern "C" int hs_default_options(hs_options* opt) {
   opt->sep_rhs_per_cta = 0;
   opt->two_front = 1;
   opt->buffer_rows = 0;
+  opt->async_setup = 0;
   return HS_OK;
 }
 
@@ -189,6 +190,7 @@ extern "C" int hs_destroy(hs_plan* plan) {
   if (!plan) return HS_OK;
   Plan* p = reinterpret_cast<Plan*>(plan);
   cudaDeviceSynchronize();
+  if (p->ready) cudaEventDestroy(p->ready);
   forget_batch_graphs(p->uid);
   release_sweep_graphs(*p);
   release_plan3(*p);
@@ -219,6 +221,7 @@ extern "C" long long hs_kernel_launches(void) { return hs::g_launches.load(); }
 extern "C" int hs_last_device_status(hs_plan* plan) {
   if (!plan) return HS_EINVAL;
   Plan* p = reinterpret_cast<Plan*>(plan);
+  plan_wait_host(*p);
   int st[3] = {0, 0, 0};
   if (cudaMemcpy(st, p->d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return HS_ECUDA;
   return st[0];
@@ -226,6 +229,7 @@ extern "C" int hs_last_device_status(hs_plan* plan) {
 
 extern "C" int hs_sync(hs_plan* plan, void* stream) {
   if (!plan) return HS_EINVAL;
+  plan_wait_host(*reinterpret_cast<Plan*>(plan));
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_status(e);
   return hs_last_device_status(plan);
@@ -323,6 +327,7 @@ static int prepare_plan(const double* c, double omega, int n, int dim, int pml_w
   if (opt_in) opt = *opt_in;
   if (opt.two_front != 0 && opt.two_front != 1) return HS_EINVAL;
   if (opt.buffer_rows < 0) return HS_EINVAL;
+  if (opt.async_setup != 0 && opt.async_setup != 1) return HS_EINVAL;
   if (opt.two_front) {
     if (n < 3 || n % 2 != 1 || pml_width < 1 || 2 * pml_width + 1 > n) return HS_EINVAL;
     // the middle layer's window must fit inside the grid
@@ -526,7 +531,7 @@ static void drop_plan(Plan* p) {
 }
 
 // Factor the prepared plans together and check their status words.
-static int factor_plans(std::vector<Plan*>& ps, cudaStream_t s) {
+static int factor_plans(std::vector<Plan*>& ps, cudaStream_t s, bool async = false) {
   std::vector<Plan*> p2;
   for (Plan* p : ps) {
     if (p->dim == 3) {
@@ -536,8 +541,17 @@ static int factor_plans(std::vector<Plan*>& ps, cudaStream_t s) {
       p2.push_back(p);
     }
   }
-  int st = launch_setup(p2, s);
+  int st = launch_setup(p2, s, async);
   if (st != HS_OK) return st;
+  if (async) {
+    // later calls order themselves after this event; the status word is read
+    // by the next synchronising call
+    for (Plan* p : ps) {
+      if (cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming) != cudaSuccess) return HS_ECUDA;
+      if (cudaEventRecord(p->ready, s) != cudaSuccess) return HS_ECUDA;
+    }
+    return HS_OK;
+  }
   for (Plan* p : ps) {
     int dst[3];
     if (cudaMemcpy(dst, p->d_status, sizeof(dst), cudaMemcpyDeviceToHost) != cudaSuccess) return HS_ECUDA;
@@ -554,7 +568,7 @@ extern "C" int hs_setup(const double* c, double omega, int n, int dim, int pml_w
   int st = prepare_plan(c, omega, n, dim, pml_width, moving_pml_width, opt, &p);
   if (st != HS_OK) return st;
   std::vector<Plan*> ps{p};
-  st = factor_plans(ps, (cudaStream_t)stream);
+  st = factor_plans(ps, (cudaStream_t)stream, dim == 2 && p->opt.async_setup == 1);
   if (st != HS_OK) { drop_plan(p); return st; }
   *out = reinterpret_cast<hs_plan*>(p);
   return HS_OK;

@@ -1287,6 +1287,7 @@ extern "C" int hs_apply(hs_plan* plan, const void* r, void* z, int nrhs, int dty
   Plan& p = *reinterpret_cast<Plan*>(plan);
   if (nrhs < 1 || nrhs > p.max_nrhs || (dtype != HS_C64 && dtype != HS_C128)) return HS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  plan_wait(p, s);
   const int n2 = (int)p.npts();
   int st = layout_to_internal(r, dtype, p.d_u, p.prec, n2, nrhs, s);
   if (st == HS_OK) st = sweep_internal(p, nrhs, s, p.opt.graphs != 0);

@@ -33,7 +33,7 @@ class HsOptions(ctypes.Structure):
                 ("restart", ctypes.c_int), ("reorth", ctypes.c_int), ("spin_budget", ctypes.c_longlong),
                 ("graphs", ctypes.c_int), ("krylov_basis", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("frontal_gemm", ctypes.c_int), ("tune_cache", ctypes.c_char_p), ("sep_rhs_per_cta", ctypes.c_int),
-                ("two_front", ctypes.c_int), ("buffer_rows", ctypes.c_int)]
+                ("two_front", ctypes.c_int), ("buffer_rows", ctypes.c_int), ("async_setup", ctypes.c_int)]
 
 
 class HsSolveInfo(ctypes.Structure):

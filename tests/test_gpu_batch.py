@@ -249,3 +249,34 @@ def test_expired_device_wait_is_reported_and_context_stays_usable():
         assert relerr(z.astype(np.complex128), ref) <= 1e-4
     finally:
         hs.hs_destroy(good)
+
+
+def test_async_setup_orders_every_later_call():
+    """async_setup = 1: hs_setup returns once the factorisation is queued on
+    its stream.  An application issued at once on another stream, a solve
+    and the status read order themselves after it: the application equals the
+    synchronously set up plan's bit for bit, and the solve converges."""
+    n, R = 127, 4
+    c = I.random_velocity(n, 11)
+    s_setup, s_use = torch.cuda.Stream(), torch.cuda.Stream()
+    sync_plan = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(max_nrhs=R, graphs=0))
+    async_plan = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(max_nrhs=R, graphs=0, async_setup=1),
+                             stream=s_setup)
+    try:
+        r = torch.from_numpy(I.random_rhs(n, R, 12)).to("cuda").to(torch.complex64)
+        torch.cuda.synchronize()
+        z_async, z_sync = torch.empty_like(r), torch.empty_like(r)
+        hs.hs_apply(async_plan, r, z_async, R, hs.HS_C64, stream=s_use)
+        hs.hs_apply(sync_plan, r, z_sync, R, hs.HS_C64)
+        torch.cuda.synchronize()
+        assert hs.hs_last_device_status(async_plan) == hs.HS_OK
+        assert torch.equal(z_async, z_sync)
+        f = torch.from_numpy(I.point_sources(n, R, 13, BP)).to("cuda")
+        u = torch.zeros_like(f)
+        torch.cuda.synchronize()     # f and u were made on the default stream
+        code, info = hs.hs_solve(async_plan, f, u, R, 1e-6, 100, stream=s_use)
+        assert code == hs.HS_OK and info["max_relres"] <= 1e-6
+        assert hs.hs_sync(async_plan, s_use) == hs.HS_OK
+    finally:
+        hs.hs_destroy(async_plan)
+        hs.hs_destroy(sync_plan)

@@ -71,6 +71,9 @@ def test_setup_rejects_bad_velocity_and_options(lib):
     assert lib.hs_setup(c.ctypes.data, 10.0, n, 2, 3, 3, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EINVAL
     o = hs.hs_default_options(sep_rhs_per_cta=3)          # 1, 2 or 4 RHS per separator-solve CTA (or 0)
     assert lib.hs_setup(c.ctypes.data, 10.0, n, 2, 3, 3, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EINVAL
+    o = hs.hs_default_options(async_setup=2)               # 0 or 1
+    assert lib.hs_setup(c.ctypes.data, 10.0, n, 2, 3, 3, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EINVAL
+    assert hs.hs_default_options().async_setup == 0
     o = hs.hs_default_options()
     assert lib.hs_setup(c.ctypes.data, 10.0, n, 4, 3, 3, ctypes.byref(o), None, ctypes.byref(plan)) == hs.HS_EINVAL
     # 3D: sizes are checked before the n^3 velocities are read
