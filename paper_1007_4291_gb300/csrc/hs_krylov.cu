@@ -211,7 +211,28 @@ __global__ void __launch_bounds__(KT) update_kernel(const typename AR::V* __rest
   typename AR::N nrm;
   AR::norm_zero(nrm);
   if (r < R) {
-    for (long long pt = (long long)blockIdx.x * 8 + warp; pt < npts; pt += (long long)gridDim.x * 8) {
+    // up to 4 vectors: two points per iteration, all loads of both issued
+    // before the products (the larger instantiations would give up resident
+    // CTAs for it)
+    const long long stride = (long long)gridDim.x * 8;
+    long long pt = (long long)blockIdx.x * 8 + warp;
+    for (; MAXJ <= 4 && pt + stride < npts; pt += 2 * stride) {
+      const long long e0 = pt * R + r, e1 = (pt + stride) * R + r;
+      typename AR::V w0 = w[e0], w1 = w[e1];
+      typename AR::V v0[MAXJ], v1[MAXJ];
+#pragma unroll
+      for (int i = 0; i < MAXJ; ++i)
+        if (i < nv) { v0[i] = V[i * vstride + e0]; v1[i] = V[i * vstride + e1]; }
+#pragma unroll
+      for (int i = 0; i < MAXJ; ++i)
+        if (i < nv) { AR::sub_prod(w0, hc[i], v0[i]); AR::sub_prod(w1, hc[i], v1[i]); }
+      w[e0] = w0;
+      w[e1] = w1;
+      if (wcopy) { wcopy[e0] = w0; wcopy[e1] = w1; }
+      AR::norm_acc(nrm, w0);
+      AR::norm_acc(nrm, w1);
+    }
+    for (; pt < npts; pt += stride) {
       const long long e = pt * R + r;
       typename AR::V wv = w[e];
 #pragma unroll
