@@ -160,7 +160,7 @@ def config_dict(args, wl):
                    else "double-float Arnoldi basis, iterate and residual" if args.prec == 64 else "FP64 throughout"),
         "l2": "inputs larger than L2 (f is %.1f GB, factors and Krylov basis tens of GB)" %
               (wl["f"].nbytes / 1e9),
-        "step": "hs_setup + hs_solve (+ hs_destroy)",
+        "step": "hs_setup (async_setup = 1) + hs_solve (+ hs_destroy)",
     }
 
 
