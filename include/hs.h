@@ -352,7 +352,11 @@ long long hs_plan_bytes(const hs_plan* plan);
  * preconditioned vectors of nrhs RHS) from one device buffer shared by the
  * whole process; it grows on demand and is kept between calls so that
  * repeated solves do not reallocate.  Solves from several host threads take
- * turns on it.  hs_release_workspace() frees it (no solve may be running).
+ * turns on it.  hs_release_workspace() frees it (no solve may be running),
+ * and also returns to the device the memory that destroyed 2D plans left in
+ * the library's plan pool (plan buffers come from a stream-ordered pool that
+ * keeps freed memory, so that setting up a new plan after destroying one does
+ * not map its memory again).
  */
 int hs_release_workspace(void);
 

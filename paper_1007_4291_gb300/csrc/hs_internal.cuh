@@ -161,6 +161,10 @@ int capture_graph(cudaStream_t cap, F&& body, cudaGraphExec_t* exec, long long* 
 // factor every block of every plan of `ps` (same factor precision): one
 // launch over all chunks, one over all reduced systems; synchronises `s`
 int launch_setup(const std::vector<Plan*>& ps, cudaStream_t s, bool async = false);
+// Stream-ordered memory pool of the 2D plan buffers of device dev (created on
+// first use, keeps freed memory), and the trim that returns that memory.
+int plan_pool(int dev, cudaMemPool_t* out);
+void trim_plan_pools();
 // Order work on stream s after an asynchronous setup of plan p (no-op once
 // the plan was set up synchronously).
 inline void plan_wait(const Plan& p, cudaStream_t s) {

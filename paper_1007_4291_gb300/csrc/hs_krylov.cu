@@ -1200,5 +1200,6 @@ extern "C" int hs_release_workspace(void) {
   if (kp.base) cudaFree(kp.base);
   kp.base = nullptr;
   kp.bytes = 0;
+  trim_plan_pools();
   return HS_OK;
 }

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <complex>
 #include <atomic>
+#include <mutex>
 #include "hs_internal.cuh"
 #include "hs_device.cuh"
 #include "hs3d.cuh"
@@ -55,13 +56,53 @@ double sigma_moving(double d, double eta_b, double C) {
 zc inv_stretch(double sig, double omega) { return zc(1.0, sig / omega); }
 zc stretch(double sig, double omega) { return 1.0 / inv_stretch(sig, omega); }
 
+// 2D plans draw their device buffers from one stream-ordered pool per device
+// that keeps freed memory (release threshold at its maximum): a plan set up
+// after another one destroyed reuses its memory without mapping it again
+// (n = 2047, 64 RHS: cudaMalloc + cudaFree of a plan's buffers 6.1 ms, from
+// the warm pool 0.06 ms).  hs_release_workspace() returns it to the device.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_plan_pool[kMaxPoolDevices] = {};
+}  // namespace
+
+int plan_pool(int dev, cudaMemPool_t* out) {
+  if (dev < 0 || dev >= kMaxPoolDevices) return HS_EUNSUPPORTED;
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  if (!g_plan_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) { cudaGetLastError(); return HS_ECUDA; }
+    unsigned long long keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_plan_pool[dev] = pool;
+  }
+  *out = g_plan_pool[dev];
+  return HS_OK;
+}
+
+void trim_plan_pools() {
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  for (int d = 0; d < kMaxPoolDevices; ++d)
+    if (g_plan_pool[d]) cudaMemPoolTrimTo(g_plan_pool[d], 0);
+}
+
+namespace {
+
 c128 to_c(zc z) { return c128{z.real(), z.imag()}; }
 c64 to_f(zc z) { return c64{(float)z.real(), (float)z.imag()}; }
 
 template <typename T> int dalloc(Plan& p, T** ptr, size_t count) {
   size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc((void**)ptr, bytes);
-  if (e != cudaSuccess) { *ptr = nullptr; return cuda_status(e); }
+  cudaMemPool_t pool = nullptr;
+  int st = plan_pool(p.device, &pool);
+  if (st != HS_OK) { *ptr = nullptr; return st; }
+  cudaError_t e = cudaMallocFromPoolAsync((void**)ptr, bytes, pool, 0);
+  if (e != cudaSuccess) { *ptr = nullptr; cudaGetLastError(); return HS_ENOMEM; }
   p.bytes += (long long)bytes;
   return HS_OK;
 }
@@ -183,7 +224,9 @@ static void free_plan_memory(Plan* p) {
                   p->k_inv_s1, p->k_a1, p->k_inv_s2, p->k_a2, p->k_m0,
                   p->d_fac, p->d_red, p->d_cor, p->d_u, p->d_z, p->d_rc, p->d_lc, p->d_xs, p->d_ps,
                   p->d_status};
-  for (void* q : ptrs) if (q) cudaFree(q);
+  // back to the plan pool, stream-ordered after everything already queued on
+  // the legacy stream (the caller has synchronised the device)
+  for (void* q : ptrs) if (q) cudaFreeAsync(q, 0);
 }
 
 extern "C" int hs_destroy(hs_plan* plan) {
@@ -532,6 +575,9 @@ static void drop_plan(Plan* p) {
 
 // Factor the prepared plans together and check their status words.
 static int factor_plans(std::vector<Plan*>& ps, cudaStream_t s, bool async = false) {
+  // the plan buffers were allocated stream-ordered on the legacy stream: the
+  // setup kernels on `s` (and every later call) come after them
+  if (cudaStreamSynchronize(0) != cudaSuccess) return HS_ECUDA;
   std::vector<Plan*> p2;
   for (Plan* p : ps) {
     if (p->dim == 3) {
