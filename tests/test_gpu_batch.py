@@ -280,3 +280,22 @@ def test_async_setup_orders_every_later_call():
     finally:
         hs.hs_destroy(async_plan)
         hs.hs_destroy(sync_plan)
+
+
+def test_plan_memory_is_reused_and_released():
+    """Plans draw their buffers from a pool that keeps freed memory: a plan
+    set up after another was destroyed (warm pool), and one set up after
+    hs_release_workspace returned the pool's memory, give the same result."""
+    n, R = 95, 3
+    c = I.random_velocity(n, 14)
+    r = torch.from_numpy(I.random_rhs(n, R, 15)).to("cuda").to(torch.complex64)
+    outs = []
+    for release in (False, False, True):
+        if release:
+            assert hs.hs_release_workspace() == hs.HS_OK
+        p = hs.hs_setup(c.ravel(), omega_of(n), n, 2, BP, BP, opts(max_nrhs=R, graphs=0))
+        try:
+            outs.append(apply_direct(p, r, R).clone())
+        finally:
+            hs.hs_destroy(p)
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
