@@ -192,8 +192,7 @@ __device__ __forceinline__ void chunk_item(const FactorArgs& a, const int bi, co
   C* bufA = reinterpret_cast<C*>(smem_raw);
   C* bufG = bufA + W * LD;
   C* bufW = bufG + W * LD;
-  C* bufT = bufW + W * LD;
-  C* cv = bufT + W * LD;
+  C* cv = bufW + W * LD;
   c128* s2 = reinterpret_cast<c128*>(cv + 2 * W);
   int* piv = reinterpret_cast<int*>(s2 + 3 * 32);
   const int lane = threadIdx.x;
@@ -210,7 +209,10 @@ __device__ __forceinline__ void chunk_item(const FactorArgs& a, const int bi, co
     const bool has_left = k > 0, has_right = k < a.P - 1;
     for (int t = lane; t < 3 * d.w; t += 32) s2[t] = a.s2win[d.s2_off + t];
     __syncwarp();
-    C *A = bufA, *G = bufG, *Wsp = bufW, *Tm = bufT;
+    // three work matrices: A (the column being factored), G (the previous
+    // column's inverse) and the spike; the spike update of pass 2 stages
+    // (S^R_j)^{-1} in A's buffer, which is free until the column is built
+    C *A = bufA, *G = bufG, *Wsp = bufW;
     bool ok = true;
 
     // Pass 1: right-to-left factorisation of the interior, for the spike.
@@ -234,6 +236,7 @@ __device__ __forceinline__ void chunk_item(const FactorArgs& a, const int bi, co
       if (lane < W) cv[W + lane] = (j > l) ? coupling<R>(a, d, s2, j - 1, lane) : C{0, 0};
       __syncwarp();
       if (has_left) {
+        C* Tm = A;
         if (lane < W) {
 #pragma unroll 4
           for (int q = 0; q < W; ++q) Tm[lane * LD + q] = slot[lane * LDP + q];
@@ -258,7 +261,8 @@ __device__ __forceinline__ void chunk_item(const FactorArgs& a, const int bi, co
           }
           __syncwarp();
         }
-        C* t = Wsp; Wsp = Tm; Tm = t;    // Wsp = W_j
+        A = Wsp;                         // the previous spike's buffer is free now
+        Wsp = Tm;                        // Wsp = W_j
         store_rows<R, W>(slot + (long long)W * LDP, Wsp, lane, d.out_off, d.d_out, LDP);
         if (j == l) store_rows<R, W>(cor + (long long)W * LD, Wsp, lane, 0, W, LD);
         if (j == r) store_rows<R, W>(cor + 2LL * W * LD, Wsp, lane, 0, W, LD);
@@ -476,9 +480,12 @@ __global__ void __launch_bounds__(32) factor_reduced_kernel(const FactorArgs* pr
 }
 
 template <typename R>
-size_t factor_smem(int W) {
-  return 4 * sizeof(cplx<R>) * W * (W + 1) + 2 * sizeof(cplx<R>) * W + 3 * 32 * sizeof(c128) + 32 * sizeof(int);
+size_t factor_smem(int W, int nmat) {
+  return nmat * sizeof(cplx<R>) * W * (W + 1) + 2 * sizeof(cplx<R>) * W + 3 * 32 * sizeof(c128) + 32 * sizeof(int);
 }
+// work matrices: three for a chunk, four for a reduced system (fewer shared
+// bytes per one-warp CTA leave room for more resident CTAs)
+constexpr int kChunkMats = 3, kReducedMats = 4;
 
 template <typename R>
 int launch_setup_t(const std::vector<Plan*>& ps, cudaStream_t s, bool async) {
@@ -518,9 +525,9 @@ int launch_setup_t(const std::vector<Plan*>& ps, cudaStream_t s, bool async) {
   cudaMemcpyAsync(d_args, args.data(), args.size() * sizeof(FactorArgs), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(d_items, items.data(), ibytes, cudaMemcpyHostToDevice, s);
   if (rbytes) cudaMemcpyAsync(d_red, reduced.data(), rbytes, cudaMemcpyHostToDevice, s);
-  const size_t smem = factor_smem<R>(Wmax);
+  const size_t smem = factor_smem<R>(Wmax, kChunkMats), smem_r = factor_smem<R>(Wmax, kReducedMats);
   cudaFuncSetAttribute(factor_chunks_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(factor_reduced_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(factor_reduced_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -534,7 +541,7 @@ int launch_setup_t(const std::vector<Plan*>& ps, cudaStream_t s, bool async) {
   if (e == cudaSuccess && !reduced.empty()) {
     const int g2 = (int)std::min<long long>((long long)reduced.size(), (long long)sms * 16);
     note_launch();
-    factor_reduced_kernel<R><<<g2, 32, smem, s>>>(d_args, d_red, (int)reduced.size());
+    factor_reduced_kernel<R><<<g2, 32, smem_r, s>>>(d_args, d_red, (int)reduced.size());
     e = cudaGetLastError();
   }
   cudaFreeAsync(buf, s);
