@@ -132,10 +132,12 @@ __global__ void __launch_bounds__(KT) dots_kernel(const typename AR::V* __restri
   typename AR::N nrm;
   AR::norm_zero(nrm);
   if (r < R) {
-    // two points per iteration, so that the loads of both are in flight together
+    // two points per iteration with every load of both issued before the
+    // products (up to 16 vectors; n = 2047, 64 RHS, 9 vectors: 3.0 ms against
+    // 13.8 ms one point at a time, where the loads queue behind the products)
     const long long stride = (long long)gridDim.x * 8;
     long long pt = (long long)blockIdx.x * 8 + warp;
-    for (; pt + stride < npts; pt += 2 * stride) {
+    for (; MAXJ <= 16 && pt + stride < npts; pt += 2 * stride) {
       const long long e0 = pt * R + r, e1 = (pt + stride) * R + r;
       const typename AR::V w0 = w[e0], w1 = w[e1];
       typename AR::V v0[MAXJ], v1[MAXJ];
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(KT) dots_kernel(const typename AR::V* __restri
       for (int i = 0; i < MAXJ; ++i)
         if (i < nv) { AR::acc_conj(acc[i], v0[i], w0); AR::acc_conj(acc[i], v1[i], w1); }
     }
-    if (pt < npts) {
+    for (; pt < npts; pt += stride) {
       const long long e = pt * R + r;
       const typename AR::V wv = w[e];
       AR::norm_acc(nrm, wv);
@@ -211,12 +213,12 @@ __global__ void __launch_bounds__(KT) update_kernel(const typename AR::V* __rest
   typename AR::N nrm;
   AR::norm_zero(nrm);
   if (r < R) {
-    // up to 4 vectors: two points per iteration, all loads of both issued
-    // before the products (the larger instantiations would give up resident
-    // CTAs for it)
+    // two points per iteration with every load of both issued before the
+    // products (up to 16 vectors; n = 2047, 64 RHS, 5-8 vectors: 2.6-3.4 ms
+    // against 3.2-4.4 ms one point at a time)
     const long long stride = (long long)gridDim.x * 8;
     long long pt = (long long)blockIdx.x * 8 + warp;
-    for (; MAXJ <= 4 && pt + stride < npts; pt += 2 * stride) {
+    for (; MAXJ <= 16 && pt + stride < npts; pt += 2 * stride) {
       const long long e0 = pt * R + r, e1 = (pt + stride) * R + r;
       typename AR::V w0 = w[e0], w1 = w[e1];
       typename AR::V v0[MAXJ], v1[MAXJ];
@@ -344,7 +346,29 @@ __global__ void __launch_bounds__(KT) xcorrect_kernel(const c64* __restrict__ Z,
     const c128 v = (i < k) ? y[i * R + r] : c128{0, 0};
     yc[i] = c64{(float)v.re, (float)v.im};
   }
-  for (long long pt = (long long)blockIdx.x * 8 + warp; pt < npts; pt += (long long)gridDim.x * 8) {
+  // two points per iteration with every load of both issued before the
+  // products (up to 16 vectors), then single points
+  const long long stride = (long long)gridDim.x * 8;
+  long long pt = (long long)blockIdx.x * 8 + warp;
+  for (; MAXJ <= 16 && pt + stride < npts; pt += 2 * stride) {
+    const long long e0 = pt * R + r, e1 = (pt + stride) * R + r;
+    c64 z0[MAXJ], z1[MAXJ];
+#pragma unroll
+    for (int i = 0; i < MAXJ; ++i)
+      if (i < k) { z0[i] = Z[i * zstride + e0]; z1[i] = Z[i * zstride + e1]; }
+    cdf x0 = x[e0], x1 = x[e1];
+    c64 d0{0.f, 0.f}, d1{0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < MAXJ; ++i)
+      if (i < k) { cfma(d0, yc[i], z0[i]); cfma(d1, yc[i], z1[i]); }
+    x0.re = df_add(x0.re, df{d0.re, 0.f});
+    x0.im = df_add(x0.im, df{d0.im, 0.f});
+    x1.re = df_add(x1.re, df{d1.re, 0.f});
+    x1.im = df_add(x1.im, df{d1.im, 0.f});
+    x[e0] = x0;
+    x[e1] = x1;
+  }
+  for (; pt < npts; pt += stride) {
     const long long e = pt * R + r;
     c64 d{0.f, 0.f};
 #pragma unroll
@@ -636,9 +660,10 @@ struct Solver {
     if (nv <= 1) dots_kernel<AR, 1><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
     else if (nv <= 4) dots_kernel<AR, 4><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
     else if (nv <= 8) dots_kernel<AR, 8><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
+    else if (nv <= 12) dots_kernel<AR, 12><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
     else if (nv <= 16) dots_kernel<AR, 16><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
     else dots_kernel<AR, 32><<<g, KT, 0, s>>>(Vb, vs, nv, v, npts, R, w.part);
-    const int mj = (nv <= 1) ? 1 : (nv <= 4) ? 4 : (nv <= 8) ? 8 : (nv <= 16) ? 16 : 32;
+    const int mj = (nv <= 1) ? 1 : (nv <= 4) ? 4 : (nv <= 8) ? 8 : (nv <= 12) ? 12 : (nv <= 16) ? 16 : 32;
     note_launch();
     reduce_parts_kernel<<<((nv + 1) * R + 255) / 256, 256, 0, s>>>(w.part, nctas, mj + 1, nv + 1, R, w.h);
   }
@@ -648,6 +673,7 @@ struct Solver {
     note_launch();
     if (nv <= 4) update_kernel<AR, 4><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part, iscale, vcopy);
     else if (nv <= 8) update_kernel<AR, 8><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part, iscale, vcopy);
+    else if (nv <= 12) update_kernel<AR, 12><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part, iscale, vcopy);
     else if (nv <= 16) update_kernel<AR, 16><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part, iscale, vcopy);
     else update_kernel<AR, 32><<<g, KT, 0, s>>>(Vb, vs, nv, w.h, v, npts, R, w.part, iscale, vcopy);
     note_launch();
@@ -1135,6 +1161,7 @@ int solve_refine(Plan& p, const void* f, void* u, int nrhs, double tol, int maxi
       const dim3 g = K.grid();
       note_launch();
       if (k <= 8) xcorrect_kernel<8><<<g, KT, 0, s>>>(Z, (long long)vs, k, w.h, x, (long long)npts, R);
+      else if (k <= 12) xcorrect_kernel<12><<<g, KT, 0, s>>>(Z, (long long)vs, k, w.h, x, (long long)npts, R);
       else if (k <= 16) xcorrect_kernel<16><<<g, KT, 0, s>>>(Z, (long long)vs, k, w.h, x, (long long)npts, R);
       else xcorrect_kernel<32><<<g, KT, 0, s>>>(Z, (long long)vs, k, w.h, x, (long long)npts, R);
     }
