@@ -21,8 +21,10 @@
 // the vector carried from column to column goes through shared memory, one
 // named barrier per column.  Per-column factor payloads (G_j | W_j rows |
 // c_j) stream into a shared-memory ring with 1D TMA bulk copies completed on
-// mbarriers (bounded waits -> HS_ETIMEOUT).  Phase 2: one or a few RHS per
-// CTA, two chain warps per RHS (see below).
+// mbarriers (bounded waits -> HS_ETIMEOUT), issued by two producer warps that
+// take the columns in turn.  Phase 2: one or a few RHS per CTA, two chain
+// warps per half chain of each RHS (complex64; one for complex128), two
+// producer warps per half (see below).
 #include <algorithm>
 #include "hs_internal.cuh"
 #include "hs_device.cuh"
@@ -157,8 +159,8 @@ __device__ __forceinline__ void ring_producer(uint64_t* full, uint64_t* empty, i
 // Each consumer thread owns a tile of ROWS window rows x RPT RHS; the
 // per-column product (W x W) * (W x RG) reads G_j from the TMA ring and the
 // vector being carried from shared memory (written by its owners before a
-// named barrier), so every column costs one barrier.  A producer warp streams
-// the column payloads.
+// named barrier), so every column costs one barrier.  Two producer warps
+// stream the column payloads.
 // SM: the small tile for at most 16 right-hand sides: CTAs of 16 RHS, one
 // window row per thread, so that the per-column chain of a thread (which sets
 // the pace when few warps share an SM) is a third as long.
@@ -459,7 +461,7 @@ __global__ void __launch_bounds__(Tile13<R, W, SM>::NCONS + 32 * P13) phase1_ker
 // so each keeps the chain variable it needs in its own registers and
 // shared-memory copy.  rho_k = -(rc_k + lc_{k+1}) is gathered into shared
 // memory first.  The four warps of a RHS meet twice on a named barrier
-// (psi'_{m+1}, then x_m); each half has its own producer warp streaming the
+// (psi'_{m+1}, then x_m); each half has its own producer warps streaming the
 // separator factors through an S2-deep TMA ring in the order its chain uses
 // them.
 // RHS per CTA (wpc, from the block size): one while the RHS of both fronts
