@@ -24,6 +24,9 @@ band LU, dense solve) as steps:
   (Algorithms 5 and 6) with exact sparse solves of each slab problem.
 * ``cnn``         -- FP64 reference of the 3-layer convolutional
   post-correction (forward, backward, Adam).
+* ``polar``       -- the scattering problem of Sec. 3 (sound-soft disk, polar
+  grid periodic in theta, radial PML) and its radial sweep (Algorithms 3 and 4
+  on rings); the CUDA library has no counterpart for this variant.
 
 Each function's docstring states the passage it follows and the readings
 of passages the paper leaves open; the tests pin every function against
