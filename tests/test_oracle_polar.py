@@ -102,3 +102,19 @@ def test_sweep_preconditions_the_table_2drad_problem(field):
     bare = P.RadialSweep(g, om, 8, 1, 4, C)
     _, it_bare, _ = K.fgmres(lambda v: bare.A.A @ v, bare.apply, rhs, tol=1e-3, restart=30, maxit=40)
     assert it_bare >= 40
+
+
+@pytest.mark.parametrize("field", ["green", "plane"])
+def test_sweep_preconditions_the_second_table_2drad_row(field):
+    """Second row of Table 2DRAD (omega/2pi = 32, 90 x 805) with PML and
+    moving PML 1.5 wavelengths wide (b_p = b = d = 12): within the paper's 7
+    iterations.  (One wavelength, b_p = b = d = 8, takes 11 here.)"""
+    f2pi = 32.0
+    g = P.PolarGrid.for_frequency(f2pi, 8)
+    om = 2 * np.pi * f2pi
+    uinc = P.point_source_field(g, om, g.r0) if field == "green" else P.plane_wave(g, om, g.r0)
+    sw = P.RadialSweep(g, om, 12, 12, 12, C)
+    rhs = P.disk_rhs(sw.A, -uinc)
+    x, it, _ = K.fgmres(lambda v: sw.A.A @ v, sw.apply, rhs, tol=1e-3, restart=30, maxit=200)
+    assert it <= 7
+    assert np.linalg.norm(rhs - sw.A.A @ x) <= 1e-3 * np.linalg.norm(rhs)
