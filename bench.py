@@ -67,11 +67,12 @@ def parse():
                          "0: double-float basis")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the comparator (complex128 sweep-GMRES), batched and 3D sections")
-    ap.add_argument("--profile", choices=["apply", "cnn", "three_d"], default=None,
+    ap.add_argument("--profile", choices=["apply", "cnn", "three_d", "solve"], default=None,
                     help="profiling driver (no JSON line): 'apply' sets up the 2D plan of --n, --dl, --nrhs "
                          "and runs --napply sweep applications; 'cnn' applies the network (tensor-core layer 2) "
                          "to --nrhs fields of --n; 'three_d' sets up the 3D plan of --n and runs --napply "
-                         "slab-sweep applications")
+                         "slab-sweep applications; 'solve' runs one hs_solve to 1e-6 of the headline's kind "
+                         "(point sources, refinement FGMRES) at --n, --dl, --nrhs")
     ap.add_argument("--napply", type=int, default=1)
     return ap.parse_args()
 
@@ -113,6 +114,17 @@ def run_profile(args):
             st = hs.hs_cnn_sync(net)
         finally:
             hs.hs_cnn_destroy(net)
+    elif args.profile == "solve":
+        c = I.random_velocity(n, 0)
+        o = hs.hs_default_options(layers_per_step=args.dl, max_nrhs=R, factor_prec=args.prec)
+        plan = hs.hs_setup(c.ravel(), 2 * np.pi * (n + 1) / 16, n, 2, 12, 12, o)
+        try:
+            f = torch.from_numpy(I.point_sources(n, R, 1, 12).astype(np.complex128)).to("cuda")
+            u = torch.zeros_like(f)
+            code, info = hs.hs_solve(plan, f, u, R, 1e-6, 200)
+            st = code if code != hs.HS_OK else hs.hs_last_device_status(plan)
+        finally:
+            hs.hs_destroy(plan)
     else:
         c = I.random_velocity(n, 0, dim=3)
         o = hs.hs_default_options(alpha=1.0, pml_C=20.0, layers_per_step=1, max_nrhs=R, frontal_gemm=3)
