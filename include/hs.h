@@ -363,7 +363,10 @@ int hs_release_workspace(void);
 /* Diagnostic: number of kernels libhs has launched in this process. */
 long long hs_kernel_launches(void);
 
-/* Free the plan and all device memory it owns.  NULL is accepted. */
+/* Free the plan and all device memory it owns (on the plan's device, whichever
+ * device is current; 2D plan buffers return to the library's plan pool, from
+ * which the next plan draws them, until hs_release_workspace()).  NULL is
+ * accepted. */
 int hs_destroy(hs_plan* plan);
 
 /* Static description of a status code. */

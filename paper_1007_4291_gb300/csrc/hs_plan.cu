@@ -232,13 +232,20 @@ static void free_plan_memory(Plan* p) {
 extern "C" int hs_destroy(hs_plan* plan) {
   if (!plan) return HS_OK;
   Plan* p = reinterpret_cast<Plan*>(plan);
+  // the plan's work and memory live on its own device, which need not be the
+  // caller's current one
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != p->device) cudaSetDevice(p->device);
   cudaDeviceSynchronize();
   if (p->ready) cudaEventDestroy(p->ready);
   forget_batch_graphs(p->uid);
   release_sweep_graphs(*p);
   release_plan3(*p);
   free_plan_memory(p);
+  const int dev = p->device;
   delete p;
+  if (cur >= 0 && cur != dev) cudaSetDevice(cur);
   return HS_OK;
 }
 
